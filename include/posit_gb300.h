@@ -1,0 +1,100 @@
+/*
+ * posit_gb300.h -- C ABI of the Posit(32,2) dense linear-algebra library for
+ * GB300 (sm_103a).
+ *
+ * Paper: "Evaluation of POSIT Arithmetic with Accelerators" (HPC Asia 2024).
+ *
+ * Data.  A posit word is a uint32_t bit pattern of Posit(32,2) (Sec. 2, Eq. 1:
+ * x = (-1)^s * 16^k * 2^e * 1.f).  0x00000000 is zero, 0x80000000 is NaR,
+ * 0x40000000 is 1, negation is the two's complement of the word.  Matrices
+ * are column-major: element (i, j) of X is X[i + j * ldX], ldX >= rows.
+ *
+ * Arithmetic.  Every multiply, add, divide and square root is rounded to
+ * Posit(32,2) at once (round to nearest, ties to the even pattern, saturating
+ * at minpos/maxpos, never to zero or NaR; NaR propagates; x/0 and sqrt(x<0)
+ * are NaR).  There is no fused multiply-add and no wider accumulator, and the
+ * order of the operations on every output element is fixed (documented per
+ * routine), so results are bit-exact and independent of tiling or launch
+ * shape.
+ *
+ * Memory and streams.  Every matrix, vector, pivot and info pointer is DEVICE
+ * memory owned by the caller, unless a routine says otherwise.  Calls are
+ * asynchronous and ordered on the CUDA stream `stream` (0 = legacy default
+ * stream); outputs are valid after the stream reaches the call.  Where a
+ * routine needs scratch memory it allocates it stream-ordered
+ * (cudaMallocAsync) and frees it before returning; nothing outlives a call.
+ *
+ * Return value.  0 on success.  -i when argument i (1-based, in the order of
+ * the signature) is invalid, as LAPACK's xerbla does, without aborting.
+ * POSIT_ERR_* (below) for CUDA failures.  Numerical status (singular or not
+ * positive definite matrices) is written to the device integer `info` with
+ * LAPACK's meaning, never signalled through the return value.
+ */
+#ifndef POSIT_GB300_H
+#define POSIT_GB300_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef uint32_t posit32_t;
+
+#if defined(__GNUC__)
+#define POSIT_API __attribute__((visibility("default")))
+#else
+#define POSIT_API
+#endif
+
+#define POSIT_OK 0
+#define POSIT_ERR_CUDA (-1001)    /* a kernel launch or CUDA runtime call failed */
+#define POSIT_ERR_ALLOC (-1002)   /* stream-ordered scratch allocation failed */
+#define POSIT_ERR_TIMEOUT (-1003) /* a bounded device-side wait gave up */
+#define POSIT_ERR_DEVICE (-1004)  /* no usable device */
+
+/* ---------------------------------------------------------------------------
+ * Conversion and element-wise arithmetic (the paper's Add/Mul/Div/Sqrt
+ * kernels, Sec. 4.2 / Table tabrandom: r[i] = p[i] op q[i]).
+ * ------------------------------------------------------------------------ */
+
+/* p[i] = posit nearest to x[i] (same rounding rule; NaN and +-Inf give NaR).
+   x: count doubles, p: count words; both device memory.  -3 if count < 0. */
+POSIT_API int posit_from_double(const double *x, posit32_t *p, int64_t count,
+                      cudaStream_t stream);
+
+/* x[i] = exact double value of p[i] (NaR gives a quiet NaN). */
+POSIT_API int posit_to_double(const posit32_t *p, double *x, int64_t count,
+                    cudaStream_t stream);
+
+/* Element-wise op on count words: op 0 add (p+q), 1 sub (p-q), 2 mul (p*q),
+   3 div (p/q), 4 sqrt (sqrt p; q is not read and may be NULL).
+   -1 for an unknown op, -5 if count < 0. */
+POSIT_API int posit_elementwise(int op, const posit32_t *p, const posit32_t *q,
+                      posit32_t *r, int64_t count, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Rgemm: C = alpha op(A) op(B) + beta C            (Sec. 3, Eq. GEMM_DEF)
+ *
+ * op(X) = X for 'N'/'n', X^T for 'T'/'t' (and 'C'/'c').  op(A) is m x k,
+ * op(B) is k x n, C is m x n.  lda >= max(1, rows of A as stored), likewise
+ * ldb, ldc >= max(1, m).
+ *
+ * Order per element (the reference-BLAS loop order, every op rounded):
+ *   c = (beta == 0) ? 0 : (beta == 1) ? C_ij : beta * C_ij
+ *   for l = 0 .. k-1 ascending:  t = alpha * op(B)_lj ;  c = c + t * op(A)_il
+ * beta == 0 means C is not read.  alpha == 0 or k == 0 gives C = beta C
+ * without reading A or B.  m == 0 or n == 0 returns at once.
+ * With alpha = -1 and beta = 1 this is the trailing-matrix update
+ * C_ij <- C_ij - sum_l A_il B_lj of blocked LU and Cholesky (Sec. 4.4).
+ * ------------------------------------------------------------------------ */
+POSIT_API int posit_rgemm(char transa, char transb, int64_t m, int64_t n, int64_t k,
+                posit32_t alpha, const posit32_t *A, int64_t lda,
+                const posit32_t *B, int64_t ldb, posit32_t beta,
+                posit32_t *C, int64_t ldc, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* POSIT_GB300_H */

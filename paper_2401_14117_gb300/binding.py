@@ -1,0 +1,118 @@
+"""ctypes binding of libposit_gb300.so -- argument marshalling only.
+
+Every function has the name and argument order of the C ABI declared in
+include/posit_gb300.h.  Matrix / vector arguments may be torch tensors (their
+data_ptr() is passed), plain integers (device addresses) or None (NULL).
+`stream` may be a torch.cuda.Stream, a raw cudaStream_t integer, or None for
+torch's current stream.  A nonzero return code raises PositError; the code
+is kept in its `.code` attribute.
+
+There is no fallback: if the library is not built, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+from .build import INCLUDE, LIB
+
+_lib = None
+
+c_i64 = ctypes.c_int64
+c_u32 = ctypes.c_uint32
+c_int = ctypes.c_int
+c_vp = ctypes.c_void_p
+c_char = ctypes.c_char
+
+# argument types per exported symbol (order of the C signatures)
+_SIGS = {
+    "posit_from_double": [c_vp, c_vp, c_i64, c_vp],
+    "posit_to_double": [c_vp, c_vp, c_i64, c_vp],
+    "posit_elementwise": [c_int, c_vp, c_vp, c_vp, c_i64, c_vp],
+    "posit_rgemm": [c_char, c_char, c_i64, c_i64, c_i64, c_u32, c_vp, c_i64,
+                    c_vp, c_i64, c_u32, c_vp, c_i64, c_vp],
+}
+
+
+class PositError(RuntimeError):
+    def __init__(self, func: str, code: int):
+        super().__init__(f"{func} returned {code}")
+        self.func = func
+        self.code = code
+
+
+def header_symbols() -> list[str]:
+    """Names of the functions declared in include/posit_gb300.h."""
+    names = []
+    for h in sorted(os.listdir(INCLUDE)):
+        if h.endswith(".h"):
+            with open(os.path.join(INCLUDE, h)) as f:
+                names += re.findall(r"POSIT_API\s+\w+\s+(posit_\w+)\s*\(", f.read())
+    return names
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(
+                f"{LIB} is not built; run `python -c 'import __graft_entry__ as g; g.build()'` "
+                "(the library has no CPU fallback)")
+        L = ctypes.CDLL(LIB)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    raise TypeError(f"cannot pass {type(x)} as a device pointer")
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _char(c):
+    return c.encode() if isinstance(c, str) else c
+
+
+def _check(name, rc):
+    if rc != 0:
+        raise PositError(name, rc)
+    return rc
+
+
+def posit_from_double(x, p, count, stream=None):
+    return _check("posit_from_double",
+                  lib().posit_from_double(_ptr(x), _ptr(p), count, _stream(stream)))
+
+
+def posit_to_double(p, x, count, stream=None):
+    return _check("posit_to_double",
+                  lib().posit_to_double(_ptr(p), _ptr(x), count, _stream(stream)))
+
+
+def posit_elementwise(op, p, q, r, count, stream=None):
+    return _check("posit_elementwise",
+                  lib().posit_elementwise(op, _ptr(p), _ptr(q), _ptr(r), count, _stream(stream)))
+
+
+def posit_rgemm(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream=None):
+    return _check("posit_rgemm", lib().posit_rgemm(
+        _char(transa), _char(transb), m, n, k, alpha, _ptr(A), lda, _ptr(B), ldb,
+        beta, _ptr(C), ldc, _stream(stream)))

@@ -1,0 +1,35 @@
+// internal.cuh -- helpers shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/posit_gb300.h"
+#include "posit_core.cuh"
+
+namespace posit {
+
+inline bool is_trans(char t) { return t == 'T' || t == 't' || t == 'C' || t == 'c'; }
+inline bool is_notrans(char t) { return t == 'N' || t == 'n'; }
+inline bool valid_trans(char t) { return is_trans(t) || is_notrans(t); }
+inline bool is_lower(char u) { return u == 'L' || u == 'l'; }
+inline bool is_upper(char u) { return u == 'U' || u == 'u'; }
+__host__ __device__ inline int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
+__host__ __device__ inline int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Map the most recent launch error to the library's return code.
+inline int launch_status() {
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? POSIT_OK : POSIT_ERR_CUDA;
+}
+
+// Triangle restriction of a C update: all, lower (i >= j) or upper (i <= j).
+enum Tri { TRI_FULL = 0, TRI_LOWER = 1, TRI_UPPER = 2 };
+
+// Rgemm without argument checking (used by the factorisations).
+int rgemm_launch(bool ta, bool tb, int tri, int64_t m, int64_t n, int64_t k,
+                 uint32_t alpha, const uint32_t *A, int64_t lda,
+                 const uint32_t *B, int64_t ldb, uint32_t beta, uint32_t *C,
+                 int64_t ldc, cudaStream_t stream);
+
+}  // namespace posit

@@ -1,0 +1,262 @@
+// posit_core.cuh -- Posit(32,2) scalar arithmetic for sm_103a, integer only.
+//
+// Format (Sec. 2, Eq. 1): x = (-1)^s * 16^k * 2^e * 1.f.  A word is decoded
+// once into a "pz" pair and all arithmetic runs on decoded values:
+//
+//   pz.s  scale S = 4k + e (2^S <= |x| < 2^(S+1)); zero uses PZ_SZERO,
+//         NaR uses PZ_SNAR (both far outside the +-120 range of real values)
+//   pz.m  sign in bit 31; magnitude 1.f with the hidden one at bit 30 and the
+//         fraction below it (at most 27 fraction bits, so bits 2..0 are 0)
+//
+// Every multiply and every add is rounded to Posit(32,2) at once (Sec. 2,
+// pre-/post-processing: operate in an internal format, re-encode the regime,
+// round with the new f_s).  Rounding rule (the paper gives none): round the
+// value's posit bit string to 31 bits after the sign, to nearest, ties to the
+// even pattern, saturating at minpos/maxpos.  For |S| <= 111 every exponent
+// bit fits, and this is ordinary round-to-nearest-even of the significand to
+// f_s = 28 - m fraction bits (m = regime run length); that is the fast path.
+// Values with |S| >= 112 use the bit-string encoder (pz_encode).
+//
+// Intermediate significands carry a "jam" bit: bit 0 is set when nonzero bits
+// were shifted out below it.  Rounding never keeps more than 28 bits of a
+// significand whose leading one is at bit 30, so the guard bit is at bit 2 or
+// higher and the jam bit only decides "exactly half" vs "more than half".
+#pragma once
+#include <stdint.h>
+
+#define PZ_SZERO (-(1 << 20))
+#define PZ_SNAR (1 << 22)
+#define PZ_NAR_BITS 0x80000000u
+#define PZ_ONE_BITS 0x40000000u
+
+struct pz {
+  int s;
+  uint32_t m;
+};
+
+static __device__ __forceinline__ pz pz_zero() { return pz{PZ_SZERO, 0u}; }
+static __device__ __forceinline__ pz pz_nar() { return pz{PZ_SNAR, 1u << 30}; }
+static __device__ __forceinline__ pz pz_one() { return pz{0, 1u << 30}; }
+static __device__ __forceinline__ bool pz_is_nar(pz a) { return a.s >= (PZ_SNAR >> 1); }
+static __device__ __forceinline__ bool pz_is_zero(pz a) { return (a.m & 0x7FFFFFFFu) == 0u; }
+
+// ---------------------------------------------------------------------------
+// word <-> decoded
+// ---------------------------------------------------------------------------
+
+// Sec. 2, Eq. 1: sign removed by two's-complement negation, regime run length
+// m from a count of leading ones/zeros, then 2 exponent bits (missing bits are
+// 0), then the fraction.
+static __device__ __forceinline__ pz pz_decode(uint32_t p) {
+  if (p == 0u) return pz_zero();
+  if (p == PZ_NAR_BITS) return pz_nar();
+  uint32_t sign = p & 0x80000000u;
+  uint32_t a = sign ? (0u - p) : p;
+  uint32_t x = a << 1;  // the 31 bits after the sign, left-aligned
+  uint32_t first = x >> 31;
+  int m = first ? __clz(~x) : __clz(x);  // 1..31 (x has bit 0 clear)
+  int k = first ? m - 1 : -m;
+  uint32_t rest = (x << m) << 1;  // drop the run and its terminating bit
+  int e = (int)(rest >> 30);
+  uint32_t mag = (1u << 30) | ((rest << 2) >> 2);
+  return pz{4 * k + e, sign | mag};
+}
+
+// Bit-string rounding of sign * 2^S * X / 2^30 (X: leading one at bit 30,
+// bit 0 possibly a jam bit) to a Posit(32,2) word.
+static __device__ __noinline__ uint32_t pz_encode(uint32_t sign, int S, uint32_t X) {
+  int k = S >> 2;  // floor(S / 4)
+  int e = S & 3;
+  uint32_t p;
+  if (k >= 30) {
+    p = 0x7FFFFFFFu;  // at or beyond maxpos = 2^120
+  } else if (k < -30) {
+    p = 1u;  // below 2^-120: minpos (never rounds to zero)
+  } else {
+    int L = k >= 0 ? k + 2 : 1 - k;  // regime length with terminator, 2..31
+    uint64_t reg = k >= 0 ? (((1ull << (k + 1)) - 1ull) << 1) : 1ull;
+    // string: regime (L bits) | e (2 bits) | the 30 bits of X below its lead
+    uint64_t str = (reg << 32) | ((uint64_t)e << 30) | (uint64_t)(X & 0x3FFFFFFFu);
+    // total length L + 32; keep 31 bits, the next one is the guard bit
+    p = (uint32_t)(str >> (L + 1));
+    uint32_t guard = (uint32_t)(str >> L) & 1u;
+    uint32_t sticky = (str & ((1ull << L) - 1ull)) != 0ull;
+    if (guard && (sticky || (p & 1u))) p += 1u;
+    if (p > 0x7FFFFFFFu) p = 0x7FFFFFFFu;
+    if (p == 0u) p = 1u;
+  }
+  return sign ? (0u - p) : p;
+}
+
+// Word of an already rounded decoded value (exact, no rounding happens).
+static __device__ __forceinline__ uint32_t pz_to_bits(pz a) {
+  if (pz_is_nar(a)) return PZ_NAR_BITS;
+  if (pz_is_zero(a)) return 0u;
+  return pz_encode(a.m & 0x80000000u, a.s, a.m & 0x7FFFFFFFu);
+}
+
+// Slow rounding for scales in the exponent-truncated band |S| >= 112.
+static __device__ __noinline__ pz pz_round_band(uint32_t sign, int S, uint32_t X) {
+  return pz_decode(pz_encode(sign, S, X));
+}
+
+// Round sign * 2^S * X / 2^30 (X leading one at bit 30 with jam bit, or
+// X == 0 for zero, or a NaR/zero sentinel scale) to the nearest posit, kept in
+// decoded form.
+static __device__ __forceinline__ pz pz_round(uint32_t sign, int S, uint32_t X) {
+  int km = (S >> 2) ^ (S >> 31);  // regime run length m minus 1
+  if ((unsigned)(km - 28) < (1u << 17)) return pz_round_band(sign, S, X);
+  // q = number of bits below the kept ones: 30 - f_s = 2 + m (3..30); the
+  // zero/NaR sentinels clamp to 30, which leaves X = 0 and X = 2^30 intact
+  uint32_t q = min((uint32_t)km + 3u, 30u);
+  uint32_t lsb = (X >> q) & 1u;
+  uint32_t r = X + ((1u << (q - 1)) - 1u) + lsb;
+  r &= ~((1u << q) - 1u);
+  uint32_t c = r >> 31;  // rounding carried into the next binade
+  return pz{S + (int)c, sign | (r >> c)};
+}
+
+// ---------------------------------------------------------------------------
+// arithmetic
+// ---------------------------------------------------------------------------
+
+static __device__ __forceinline__ pz pz_neg(pz a) {
+  if (pz_is_nar(a) || pz_is_zero(a)) return a;
+  return pz{a.s, a.m ^ 0x80000000u};
+}
+
+// a (x) b, one rounding.  The 28x28-bit significand product is exact in 64
+// bits; its leading one lands at bit 61 or 62.
+static __device__ __forceinline__ pz pz_mul(pz a, pz b) {
+  uint32_t A = a.m & 0x7FFFFFFFu;  // leading one at bit 30 (or 0)
+  uint32_t B = b.m << 1;           // leading one at bit 31 (or 0)
+  uint64_t P = (uint64_t)A * (uint64_t)B;
+  uint32_t hi = (uint32_t)(P >> 32), lo = (uint32_t)P;
+  uint32_t t = hi >> 30;           // 1 if the leading one is at bit 62
+  uint32_t sh = 1u - t;
+  uint32_t X = __funnelshift_l(lo, hi, sh);  // leading one to bit 30
+  uint32_t rest = lo << sh;
+  X |= min(rest, 1u);              // jam
+  int S = a.s + b.s + (int)t;
+  return pz_round((a.m ^ b.m) & 0x80000000u, S, X);
+}
+
+// c (+) t, one rounding.  Sign-magnitude add with the smaller-scale operand
+// shifted right by d (capped at 31) and its shifted-out bits jammed into
+// bit 0.  With the larger magnitude's lead at bit 30, a same-sign sum stays
+// below 2^32, and a difference is negative only when d = 0 (then exact).
+static __device__ __forceinline__ pz pz_add(pz c, pz t) {
+  bool sw = t.s > c.s;
+  int SL = sw ? t.s : c.s;
+  int SS = sw ? c.s : t.s;
+  uint32_t mL = sw ? t.m : c.m;
+  uint32_t mS = sw ? c.m : t.m;
+  uint32_t d = min((uint32_t)(SL - SS), 31u);
+  uint32_t magL = mL & 0x7FFFFFFFu;
+  uint32_t magS = mS & 0x7FFFFFFFu;
+  uint32_t shv = magS >> d;
+  uint32_t lost = __funnelshift_r(0u, magS, d);  // magS << (32 - d), 0 if d = 0
+  shv |= min(lost, 1u);
+  uint32_t sub = (mL ^ mS) >> 31;
+  uint32_t R = sub ? (magL - shv) : (magL + shv);
+  uint32_t neg = sub & (R >> 31);  // difference went negative (d = 0 only)
+  R = neg ? (0u - R) : R;
+  uint32_t sign = (mL & 0x80000000u) ^ (neg << 31);
+  int lz = __clz(R);
+  int sft = lz - 1;  // left shift putting the leading one at bit 30
+  uint32_t X = sft >= 0 ? (R << sft) : ((R >> 1) | (R & 1u));
+  int S = SL - sft;
+  S = (R == 0u) ? PZ_SZERO : S;  // exact cancellation
+  return pz_round(sign, S, X);
+}
+
+static __device__ __forceinline__ pz pz_sub(pz c, pz t) { return pz_add(c, pz_neg(t)); }
+
+// a (/) b, one rounding.  Restoring division of the significands gives 32
+// quotient bits plus a remainder test for the jam bit.
+static __device__ __noinline__ pz pz_div(pz a, pz b) {
+  if (pz_is_nar(a) || pz_is_nar(b) || pz_is_zero(b)) return pz_nar();
+  if (pz_is_zero(a)) return pz_zero();
+  uint32_t A = a.m & 0x7FFFFFFFu, B = b.m & 0x7FFFFFFFu;  // both in [2^30, 2^31)
+  // quotient of (A / B) * 2^31, bit by bit (A / B lies in (1/2, 2))
+  uint64_t rem = A;
+  uint32_t q = 0;
+  for (int i = 31; i >= 0; --i) {
+    if (rem >= B) { rem -= B; q |= 1u << i; }
+    rem <<= 1;
+  }
+  // q = floor(A * 2^31 / B) in (2^30, 2^32)
+  uint32_t jam = rem != 0ull;
+  int S = a.s - b.s;
+  uint32_t X;
+  if (q >> 31) {
+    X = (q >> 1) | (q & 1u) | jam;
+  } else {
+    X = q | jam;
+    S -= 1;
+  }
+  return pz_round((a.m ^ b.m) & 0x80000000u, S, X);
+}
+
+// sqrt(a), one rounding.  Bit-by-bit integer square root of the significand
+// scaled to 64 bits, with a remainder test for the jam bit.
+static __device__ __noinline__ pz pz_sqrt(pz a) {
+  if (pz_is_nar(a) || (a.m >> 31)) return pz_nar();
+  if (pz_is_zero(a)) return pz_zero();
+  uint32_t mag = a.m & 0x7FFFFFFFu;
+  int S = a.s;
+  uint64_t N;
+  if (S & 1) {
+    N = (uint64_t)mag << 33;  // value = N * 2^(S - 1 - 62); N in [2^63, 2^64)
+    S -= 1;
+  } else {
+    N = (uint64_t)mag << 32;  // value = N * 2^(S - 62);     N in [2^62, 2^63)
+  }
+  uint64_t r = 0;  // floor(sqrt(N)) < 2^32
+  for (int i = 31; i >= 0; --i) {
+    uint64_t t = r | (1ull << i);
+    if (t * t <= N) r = t;
+  }
+  uint32_t jam = (r * r) != N;
+  // sqrt(value) = r * 2^((S - 62) / 2), r in [2^31, 2^32): lead at bit 31
+  uint32_t r32 = (uint32_t)r;
+  uint32_t X = (r32 >> 1) | (r32 & 1u) | jam;
+  return pz_round(0u, S >> 1, X);
+}
+
+// ---------------------------------------------------------------------------
+// double <-> posit (input conversion of the harness; same rounding rule)
+// ---------------------------------------------------------------------------
+static __device__ __forceinline__ uint32_t pz_from_double(double x) {
+  uint64_t u = (uint64_t)__double_as_longlong(x);
+  uint32_t sign = (uint32_t)(u >> 32) & 0x80000000u;
+  int ex = (int)((u >> 52) & 0x7FF);
+  uint64_t man = u & ((1ull << 52) - 1ull);
+  if (ex == 0x7FF) return PZ_NAR_BITS;  // NaN, Inf
+  if (ex == 0 && man == 0) return 0u;
+  uint64_t sig;
+  int S;
+  if (ex == 0) {  // subnormal: normalise
+    int lz = __clzll(man) - 11;  // leading one to bit 52
+    sig = man << lz;
+    S = -1022 - lz;
+  } else {
+    sig = man | (1ull << 52);
+    S = ex - 1023;
+  }
+  // leading one at bit 52 -> bit 30; 22 bits shifted out go to the jam bit
+  uint32_t X = (uint32_t)(sig >> 22) | (uint32_t)((sig & ((1ull << 22) - 1ull)) != 0ull);
+  // |S| <= 1074 stays far from the zero/NaR sentinel scales; large |S|
+  // takes the band path and saturates there
+  return pz_to_bits(pz_round(sign, S, X));
+}
+
+static __device__ __forceinline__ double pz_to_double(uint32_t p) {
+  pz a = pz_decode(p);
+  if (pz_is_nar(a)) return __longlong_as_double(0x7FF8000000000000ll);
+  if (pz_is_zero(a)) return 0.0;
+  uint64_t sign = (uint64_t)(a.m >> 31) << 63;
+  uint64_t ex = (uint64_t)(a.s + 1023) << 52;
+  uint64_t man = (uint64_t)(a.m & 0x3FFFFFFFu) << 22;
+  return __longlong_as_double((long long)(sign | ex | man));
+}

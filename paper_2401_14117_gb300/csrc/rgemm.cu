@@ -1,0 +1,196 @@
+// rgemm.cu -- Posit(32,2) Rgemm, C = alpha op(A) op(B) + beta C
+// (Sec. 3, Eq. GEMM_DEF; the paper's GPU kernels, Sec. 3.2, are four
+// shared-memory-blocked kernels, one per transpose pair).
+//
+// Tensor cores do not apply: every product and every sum is rounded to
+// Posit(32,2) in a fixed order, which is not a dense FP contraction.  The
+// kernel is bound by integer instruction issue.  Per CTA:
+//   * a BM x BK tile of op(A) and a BK x BN tile of op(B) are loaded from
+//     global memory (coalesced along the contiguous dimension) and decoded
+//     ONCE into shared memory as (scale, signed significand) pairs; the B
+//     tile is pre-multiplied by alpha (t = alpha * op(B)_lj, one rounding);
+//   * each thread owns a TM x TN register tile of C, kept DECODED across the
+//     whole k loop, and applies c = c + t * a for l ascending -- TM*TN
+//     independent dependency chains per thread give the instruction-level
+//     parallelism that hides the integer pipeline latency;
+//   * C is encoded to posit words once, at the end.
+// The per-element order is exactly the reference-BLAS order, so the result
+// does not depend on BM/BN/BK or the grid.
+#include "internal.cuh"
+
+namespace posit {
+namespace {
+
+constexpr int BM = 128, BN = 64, BK = 16;
+constexpr int TM = 4, TN = 8;
+constexpr int NT = 256;  // (BM / TM) * (BN / TN)
+static_assert((BM / TM) * (BN / TN) == NT, "thread tile");
+
+template <int TRI>
+__device__ __forceinline__ bool tri_ok(int64_t i, int64_t j) {
+  return TRI == TRI_FULL || (TRI == TRI_LOWER ? i >= j : i <= j);
+}
+
+template <bool TA, bool TB, int TRI>
+__global__ void __launch_bounds__(NT, 2)
+rgemm_kernel(int64_t M, int64_t N, int64_t K, uint32_t alpha,
+             const uint32_t *__restrict__ A, int64_t lda,
+             const uint32_t *__restrict__ B, int64_t ldb, uint32_t beta,
+             uint32_t *__restrict__ C, int64_t ldc) {
+  __shared__ __align__(16) pz As[BK][BM];
+  __shared__ __align__(16) pz Bs[BK][BN];
+
+  const int tid = threadIdx.x;
+  const int tm = tid & 31;  // row group: rows tm*TM .. +TM-1
+  const int tn = tid >> 5;  // column group (one warp): cols tn*TN .. +TN-1
+  const int64_t m0 = (int64_t)blockIdx.x * BM;
+  const int64_t n0 = (int64_t)blockIdx.y * BN;
+  if (TRI == TRI_LOWER && n0 > m0 + BM - 1) return;  // tile wholly above diagonal
+  if (TRI == TRI_UPPER && m0 > n0 + BN - 1) return;  // tile wholly below diagonal
+
+  const pz alpha_d = pz_decode(alpha);
+  const pz beta_d = pz_decode(beta);
+
+  // Accumulators: padding elements (outside C or the triangle) start at 1
+  // and are never stored; they only keep the warp on the fast path.
+  pz acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      int64_t r = m0 + tm * TM + i, c = n0 + tn * TN + j;
+      pz v = pz_one();
+      if (r < M && c < N && tri_ok<TRI>(r, c)) {
+        if (beta == 0u) {
+          v = pz_zero();
+        } else {
+          v = pz_decode(C[r + c * ldc]);
+          if (beta != PZ_ONE_BITS) v = pz_mul(beta_d, v);
+        }
+      }
+      acc[i][j] = v;
+    }
+  }
+
+  const int64_t kTot = (alpha == 0u) ? 0 : K;
+  for (int64_t k0 = 0; k0 < kTot; k0 += BK) {
+    __syncthreads();  // previous tile fully consumed
+#pragma unroll
+    for (int q = 0; q < (BM * BK) / NT; ++q) {
+      int e = tid + q * NT;
+      int r, c;
+      if (!TA) { r = e % BM; c = e / BM; } else { c = e % BK; r = e / BK; }
+      int64_t gr = m0 + r, gk = k0 + c;
+      pz v = pz_one();
+      if (gr < M && gk < K) v = pz_decode(TA ? A[gk + gr * lda] : A[gr + gk * lda]);
+      As[c][r] = v;
+    }
+#pragma unroll
+    for (int q = 0; q < (BK * BN) / NT; ++q) {
+      int e = tid + q * NT;
+      int r, c;
+      if (!TB) { r = e % BK; c = e / BK; } else { c = e % BN; r = e / BN; }
+      int64_t gk = k0 + r, gc = n0 + c;
+      pz v = pz_one();
+      if (gk < K && gc < N) {
+        v = pz_decode(TB ? B[gc + gk * ldb] : B[gk + gc * ldb]);
+        if (alpha != PZ_ONE_BITS) v = pz_mul(alpha_d, v);  // t = alpha * op(B)_lj
+      }
+      Bs[r][c] = v;
+    }
+    __syncthreads();
+
+    const int kend = (int)min64(BK, K - k0);
+#pragma unroll 1
+    for (int kk = 0; kk < kend; ++kk) {
+      pz a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][tm * TM + i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tn * TN + j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) {
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = pz_add(acc[i][j], pz_mul(b[j], a[i]));
+      }
+    }
+  }
+
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      int64_t r = m0 + tm * TM + i, c = n0 + tn * TN + j;
+      if (r < M && c < N && tri_ok<TRI>(r, c)) C[r + c * ldc] = pz_to_bits(acc[i][j]);
+    }
+  }
+}
+
+template <int TRI>
+int launch_tri(bool ta, bool tb, int64_t m, int64_t n, int64_t k, uint32_t alpha,
+               const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb,
+               uint32_t beta, uint32_t *C, int64_t ldc, cudaStream_t stream) {
+  const int64_t gx = ceil_div(m, BM);
+  // gridDim.y is limited to 65535: split very wide C into column chunks
+  const int64_t max_cols = (int64_t)65535 * BN;
+  for (int64_t c0 = 0; c0 < n; c0 += max_cols) {
+    int64_t nc = min64(max_cols, n - c0);
+    dim3 grid((unsigned)gx, (unsigned)ceil_div(nc, BN));
+    const uint32_t *Bp = tb ? B + c0 : B + c0 * ldb;
+    uint32_t *Cp = C + c0 * ldc;
+    // a column chunk of a triangular update keeps its global diagonal: the
+    // chunked path is only used for TRI_FULL (n <= 4M columns otherwise)
+    if (!ta && !tb)
+      rgemm_kernel<false, false, TRI><<<grid, NT, 0, stream>>>(m, nc, k, alpha, A, lda, Bp, ldb, beta, Cp, ldc);
+    else if (!ta && tb)
+      rgemm_kernel<false, true, TRI><<<grid, NT, 0, stream>>>(m, nc, k, alpha, A, lda, Bp, ldb, beta, Cp, ldc);
+    else if (ta && !tb)
+      rgemm_kernel<true, false, TRI><<<grid, NT, 0, stream>>>(m, nc, k, alpha, A, lda, Bp, ldb, beta, Cp, ldc);
+    else
+      rgemm_kernel<true, true, TRI><<<grid, NT, 0, stream>>>(m, nc, k, alpha, A, lda, Bp, ldb, beta, Cp, ldc);
+    int st = launch_status();
+    if (st != POSIT_OK) return st;
+  }
+  return POSIT_OK;
+}
+
+}  // namespace
+
+int rgemm_launch(bool ta, bool tb, int tri, int64_t m, int64_t n, int64_t k,
+                 uint32_t alpha, const uint32_t *A, int64_t lda, const uint32_t *B,
+                 int64_t ldb, uint32_t beta, uint32_t *C, int64_t ldc,
+                 cudaStream_t stream) {
+  if (m <= 0 || n <= 0) return POSIT_OK;
+  if (tri == TRI_LOWER)
+    return launch_tri<TRI_LOWER>(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream);
+  if (tri == TRI_UPPER)
+    return launch_tri<TRI_UPPER>(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream);
+  return launch_tri<TRI_FULL>(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream);
+}
+
+}  // namespace posit
+
+using namespace posit;
+
+extern "C" int posit_rgemm(char transa, char transb, int64_t m, int64_t n, int64_t k,
+                           posit32_t alpha, const posit32_t *A, int64_t lda,
+                           const posit32_t *B, int64_t ldb, posit32_t beta,
+                           posit32_t *C, int64_t ldc, cudaStream_t stream) {
+  if (!valid_trans(transa)) return -1;
+  if (!valid_trans(transb)) return -2;
+  if (m < 0) return -3;
+  if (n < 0) return -4;
+  if (k < 0) return -5;
+  const bool ta = is_trans(transa), tb = is_trans(transb);
+  const int64_t arows = ta ? k : m, brows = tb ? n : k;
+  if (lda < max64(1, arows)) return -8;
+  if (ldb < max64(1, brows)) return -10;
+  if (ldc < max64(1, m)) return -13;
+  if (m == 0 || n == 0) return POSIT_OK;
+  if ((alpha == 0u || k == 0) && beta == PZ_ONE_BITS) return POSIT_OK;
+  const bool reads_ab = alpha != 0u && k > 0;
+  if (reads_ab && !A) return -7;
+  if (reads_ab && !B) return -9;
+  if (!C) return -12;
+  return rgemm_launch(ta, tb, TRI_FULL, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream);
+}
