@@ -80,31 +80,30 @@ def config(m, n, k):
 
 # ------------------------------------------------------------------ oracle
 def oracle_sample_rate(m, n, k, seconds, seed=20240126):
-    """The CPU oracle on whole columns of C, growing the sample to about
-    `seconds` of work.  Returns (Gflops, threads, description)."""
+    """The CPU oracle on whole columns of C (OpenMP parallelises over
+    columns, so the sample is at least one column per thread), grown until
+    one sample takes about `seconds`.  Returns (Gflops, threads, description)."""
     import numpy as np
 
     import oracle
     from paper_2401_14117_gb300 import inputs
+    threads = oracle.get_threads()
     rng = np.random.default_rng(seed)
     A = oracle.from_double_array(inputs.uniform((m, k), seed))
-    cols = 1
-    spent = 0.0
-    done_ops = 0
+    cols = min(n, threads)
     while True:
         B = oracle.from_double_array(rng.uniform(-1, 1, (k, cols)))
         C = np.zeros((m, cols), np.uint32)
         t0 = time.perf_counter()
         oracle.rgemm("N", "N", ONE, A, B, 0, C)
         dt = time.perf_counter() - t0
-        spent += dt
-        done_ops += 2 * m * cols * k
-        if spent >= seconds * 0.5 or cols >= n:
+        if dt >= seconds * 0.4 or cols >= n:
             rate = 2 * m * cols * k / dt / 1e9
-            return rate, oracle.get_threads(), (
+            return rate, threads, (
                 f"{cols} whole columns of C ({m}x{cols}x{k}, {2 * m * cols * k:.3g} posit ops) "
-                f"of the {m}x{n}x{k} product; rate of the last sample")
-        cols = min(n, max(cols * 2, int(cols * seconds * 0.6 / max(dt, 1e-3))))
+                f"of the {m}x{n}x{k} product, {dt:.1f} s")
+        grow = max(2.0, seconds * 0.6 / max(dt, 1e-3))
+        cols = min(n, threads * max(1, int(round(cols * grow / threads))))
 
 
 def run_reference(args):
@@ -117,7 +116,7 @@ def run_reference(args):
     import numpy as np
     from paper_2401_14117_gb300 import inputs
     A = oracle.from_double_array(inputs.uniform((m, k), 1))
-    cols = max(1, int(2e8 / (2 * m * k)))  # about 1-3 s of oracle work per step
+    cols = max(oracle.get_threads(), int(2e9 / (2 * m * k)))  # a few seconds of work per step
     B = oracle.from_double_array(inputs.uniform((k, cols), 2))
     C = np.zeros((m, cols), np.uint32)
     for _ in range(args.warmup):

@@ -94,6 +94,76 @@ POSIT_API int posit_rgemm(char transa, char transb, int64_t m, int64_t n, int64_
                 const posit32_t *B, int64_t ldb, posit32_t beta,
                 posit32_t *C, int64_t ldc, cudaStream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * Rgetrf: LU factorisation with partial pivoting, A = P L U     (Sec. 3, the
+ * LAPACK dgetrf the paper runs through MPLAPACK; Sec. 5.2)
+ *
+ * A: m x n (lda >= max(1, m)), overwritten by L (unit lower, below the
+ * diagonal) and U.  ipiv: min(m, n) int32, 1-based: row i was swapped with
+ * row ipiv[i] (LAPACK convention).  info: one device int32, set to 0, or to
+ * j+1 for the first column j whose pivot is exactly zero (the factorisation
+ * still completes; U is singular), or to POSIT_ERR_TIMEOUT if a bounded
+ * device wait gave up.
+ *
+ * Order: for each column c in turn -- pivot = first row of largest |a_ic|
+ * (i >= c) comparing the two's-complement absolute value of the words as
+ * unsigned integers (so NaR ranks highest); swap rows c and pivot across all
+ * columns; r = 1 / a_cc; l_ic = a_ic * r; a_ik = a_ik - l_ic * a_ck for all
+ * i, k > c.  The blocked schedule (panels of up to 256 columns, trailing
+ * update by Rgemm with alpha = -1, beta = 1) applies exactly these operations
+ * to every element in the same order, so the result is bit-identical for
+ * every block size.  Scratch: about 0.7 MB, stream-ordered.
+ * Errors: -1 m < 0, -2 n < 0, -3 A NULL, -4 lda, -5 ipiv NULL, -6 info NULL.
+ * ------------------------------------------------------------------------ */
+POSIT_API int posit_rgetrf(int64_t m, int64_t n, posit32_t *A, int64_t lda, int32_t *ipiv,
+                 int32_t *info, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Rgetrs: solve A X = B ('N') or A^T X = B ('T') with the factors of
+ * posit_rgetrf (Sec. 5.1).  B: n x nrhs (ldb >= max(1, n)), overwritten by X.
+ *
+ * Order ('N'): the ipiv swaps for i = 0 .. n-1; then L y = b with y_i
+ * receiving l_ij y_j for j = 0 .. i-1 ascending; then U x = y with x_i
+ * receiving u_ik x_k for k = n-1 .. i+1 descending, then x_i = x_i / u_ii.
+ * ('T'): U^T y = b, y_i receiving u_ki y_k for k ascending, then / u_ii;
+ * L^T z = y, z_i receiving l_ki z_k for k = i+1 .. n-1 ascending (one serial
+ * chain of n(n-1)/2 operations per column); the swaps in reverse order.
+ * These are the reference-BLAS trsm orders.  No singularity check: x / 0 is
+ * NaR.  Errors: -1 trans, -2 n, -3 nrhs, -4 A NULL, -5 lda, -6 ipiv NULL,
+ * -7 B NULL, -8 ldb.
+ * ------------------------------------------------------------------------ */
+POSIT_API int posit_rgetrs(char trans, int64_t n, int64_t nrhs, const posit32_t *A, int64_t lda,
+                 const int32_t *ipiv, posit32_t *B, int64_t ldb, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Rpotrf: Cholesky factorisation A = L L^T (uplo 'L') or U^T U ('U')
+ * (Sec. 3, LAPACK dpotrf through MPLAPACK; Sec. 5.2).
+ *
+ * Only the uplo triangle of A (n x n, lda >= max(1, n)) is read and written.
+ * Order (uplo 'L'): for each column j in turn -- d = a_jj; if d <= 0 or NaR:
+ * info = j+1 and stop (a_jj keeps d); a_jj = sqrt(d); r = 1 / a_jj;
+ * a_ij = a_ij * r (i > j); a_ik = a_ik - a_ij * a_kj for j < k <= i.  uplo
+ * 'U' is the transposed mirror.  Blocked: panels of up to 256 columns, the
+ * trailing triangle updated by Rgemm (alpha = -1, beta = 1); bit-identical
+ * for every block size.  After a failure (info > 0) columns 0 .. info-2 hold
+ * their final values and the rest of the triangle is unspecified.
+ * Errors: -1 uplo, -2 n, -3 A NULL, -4 lda, -5 info NULL.
+ * ------------------------------------------------------------------------ */
+POSIT_API int posit_rpotrf(char uplo, int64_t n, posit32_t *A, int64_t lda, int32_t *info,
+                 cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Rpotrs: solve A X = B with the factor of posit_rpotrf (Sec. 5.1).
+ * Order (uplo 'L'): L y = b, y_i receiving l_ij y_j for j ascending, then
+ * / l_ii; L^T x = y, x_i receiving l_ki x_k for k = i+1 .. n-1 ascending
+ * (the reference trsm dot form; one serial chain of n(n-1)/2 operations per
+ * column), then / l_ii.  (uplo 'U'): U^T y = b with k ascending then / u_ii;
+ * U x = y with k descending then / u_ii.  Errors: -1 uplo, -2 n, -3 nrhs,
+ * -4 A NULL, -5 lda, -6 B NULL, -7 ldb.
+ * ------------------------------------------------------------------------ */
+POSIT_API int posit_rpotrs(char uplo, int64_t n, int64_t nrhs, const posit32_t *A, int64_t lda,
+                 posit32_t *B, int64_t ldb, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -32,6 +32,10 @@ _SIGS = {
     "posit_elementwise": [c_int, c_vp, c_vp, c_vp, c_i64, c_vp],
     "posit_rgemm": [c_char, c_char, c_i64, c_i64, c_i64, c_u32, c_vp, c_i64,
                     c_vp, c_i64, c_u32, c_vp, c_i64, c_vp],
+    "posit_rgetrf": [c_i64, c_i64, c_vp, c_i64, c_vp, c_vp, c_vp],
+    "posit_rgetrs": [c_char, c_i64, c_i64, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp],
+    "posit_rpotrf": [c_char, c_i64, c_vp, c_i64, c_vp, c_vp],
+    "posit_rpotrs": [c_char, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp],
 }
 
 
@@ -116,3 +120,23 @@ def posit_rgemm(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, st
     return _check("posit_rgemm", lib().posit_rgemm(
         _char(transa), _char(transb), m, n, k, alpha, _ptr(A), lda, _ptr(B), ldb,
         beta, _ptr(C), ldc, _stream(stream)))
+
+
+def posit_rgetrf(m, n, A, lda, ipiv, info, stream=None):
+    return _check("posit_rgetrf", lib().posit_rgetrf(m, n, _ptr(A), lda, _ptr(ipiv), _ptr(info),
+                                                      _stream(stream)))
+
+
+def posit_rgetrs(trans, n, nrhs, A, lda, ipiv, B, ldb, stream=None):
+    return _check("posit_rgetrs", lib().posit_rgetrs(_char(trans), n, nrhs, _ptr(A), lda,
+                                                      _ptr(ipiv), _ptr(B), ldb, _stream(stream)))
+
+
+def posit_rpotrf(uplo, n, A, lda, info, stream=None):
+    return _check("posit_rpotrf", lib().posit_rpotrf(_char(uplo), n, _ptr(A), lda, _ptr(info),
+                                                      _stream(stream)))
+
+
+def posit_rpotrs(uplo, n, nrhs, A, lda, B, ldb, stream=None):
+    return _check("posit_rpotrs", lib().posit_rpotrs(_char(uplo), n, nrhs, _ptr(A), lda,
+                                                      _ptr(B), ldb, _stream(stream)))

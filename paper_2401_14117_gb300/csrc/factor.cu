@@ -1,0 +1,623 @@
+// factor.cu -- blocked right-looking Rgetrf (LU with partial pivoting) and
+// Rpotrf (Cholesky) on the GPU (Sec. 3: LAPACK dgetrf/dpotrf structure with
+// Rgemm as the trailing-matrix update; Sec. 5.2 runs them with only Rgemm
+// offloaded -- here every step runs on the device and the host only enqueues).
+//
+// Per panel of jb columns starting at column j:
+//   LU:   panel_kernel (LU)  pivot search, row swap inside the panel, scaling by
+//                            r = 1 / pivot, rank-1 updates of the panel columns
+//         laswp_kernel       the panel's swaps on the columns left and right
+//         trsm_llu_kernel    U12 <- L11^-1 A12 (unit lower, forward)
+//         rgemm              A22 <- A22 - L21 U12   (alpha = -1, beta = 1)
+//   Chol: panel_kernel (Chol) sqrt of the diagonal, scaling by its reciprocal,
+//                            updates of the panel's lower triangle (this also
+//                            performs the trsm of the rows below the block)
+//         rgemm (lower)      A22 <- A22 - L21 L21^T on the lower triangle
+//
+// Every element receives its updates in ascending column order, one rounded
+// multiply and one rounded subtract each, exactly as the unblocked algorithm
+// does, so the result is the same for every jb.
+//
+// The panel kernel is a cooperative launch: G CTAs own contiguous chunks of
+// the panel's rows, kept decoded in shared memory for the whole panel, and
+// meet at one grid barrier per column.  The barrier's wait is bounded (about
+// 2 s of global time); a CTA that gives up sets the error flag, writes
+// POSIT_ERR_TIMEOUT into info, and every CTA returns.
+#include <cooperative_groups.h>
+
+#include "internal.cuh"
+
+namespace posit {
+namespace {
+
+constexpr int PT = 256;           // panel kernel threads
+constexpr int TRSM_NC = 32;       // trsm columns per CTA
+constexpr int TRSM_T = 256;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded barrier wait
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid barrier over `nblocks` co-resident CTAs (cooperative launch).  bar[0]
+// counts arrivals, bar[1] is the generation.  Returns false after a timeout.
+__device__ bool grid_barrier(unsigned *bar, unsigned nblocks, int *err, int32_t *info) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *vgen = bar + 1;
+    unsigned gen = *vgen;
+    __threadfence();
+    unsigned arrived = atomicAdd(bar, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      unsigned long long t0 = global_ns();
+      while (*vgen == gen) {
+        if (*(volatile int *)err) break;
+        if (global_ns() - t0 > kWaitNs) {
+          atomicExch(err, 1);
+          atomicExch(info, POSIT_ERR_TIMEOUT);
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *(volatile int *)err == 0;
+}
+
+// |x| ordering key of a decoded value: (scale, magnitude) lexicographic, which
+// is the order of the words' two's-complement absolute values (NaR largest,
+// zero smallest).
+__device__ __forceinline__ uint64_t abs_key(pz a) {
+  return ((uint64_t)(uint32_t)(a.s + (1 << 24)) << 32) | (uint64_t)(a.m & 0x7FFFFFFFu);
+}
+
+struct PanelArgs {
+  uint32_t *A;
+  int64_t lda;
+  int64_t m;     // rows of the matrix (the panel covers rows j .. m-1)
+  int64_t j;     // first column (and first row) of the panel
+  int jb;        // panel width
+  int R;         // rows per CTA
+  int trans;     // element (i, k) at A[k + i*lda] (Cholesky, upper storage)
+  int chol;      // 0: LU with partial pivoting, 1: Cholesky
+  int32_t *ipiv;
+  int32_t *info;
+  // scratch (zeroed before the first panel)
+  unsigned *bar;
+  int *err;
+  uint64_t *cand_key;   // [2][G]
+  int64_t *cand_row;    // [2][G]
+  pz *cand_vals;        // [2][G][jb]
+  pz *xrow;             // LU: old pivot row [2][jb]; Chol: broadcast column [2][jb]
+  pz *diag;             // Chol: next diagonal value [2]
+};
+
+__device__ __forceinline__ int64_t panel_addr(const PanelArgs &a, int64_t i, int64_t k) {
+  return a.trans ? (k + i * a.lda) : (i + k * a.lda);
+}
+
+__global__ void __launch_bounds__(PT, 1) panel_kernel(PanelArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int jb = a.jb, R = a.R;
+  pz *tile = reinterpret_cast<pz *>(smem_raw);  // [R][jb]
+  pz *prow = tile + (size_t)R * jb;             // [jb]
+  __shared__ uint64_t red_key[PT / 32];
+  __shared__ int64_t red_row[PT / 32];
+  __shared__ pz s_r;   // reciprocal of the pivot / of the diagonal sqrt
+  __shared__ int s_flag;
+  __shared__ int64_t s_piv;
+
+  const int tid = threadIdx.x;
+  const int g = blockIdx.x;
+  const unsigned G = gridDim.x;
+  const int64_t row0 = a.j + (int64_t)g * R;            // first global row of this CTA
+  const int nrows = (int)max64(0, min64((int64_t)R, a.m - row0));
+
+  if (a.chol && *(volatile int32_t *)a.info != 0) return;  // an earlier panel failed
+
+  // load this CTA's rows of the panel, decoded
+  for (int idx = tid; idx < R * jb; idx += PT) {
+    int r, c;
+    if (a.trans) { c = idx % jb; r = idx / jb; } else { r = idx % R; c = idx / R; }
+    pz v = pz_zero();
+    if (r < nrows) v = pz_decode(a.A[panel_addr(a, row0 + r, a.j + c)]);
+    tile[(size_t)r * jb + c] = v;
+  }
+  __syncthreads();
+
+  if (a.chol) {
+    // diagonal value of column 0, published by the CTA owning row j
+    if (g == 0 && tid == 0) a.diag[0] = tile[0];
+    if (!grid_barrier(a.bar, G, a.err, a.info)) return;
+  }
+
+  for (int c = 0; c < jb; ++c) {
+    const int buf = c & 1;
+    const int64_t gcol = a.j + c;            // global column, = global pivot row
+    const int owner_c = (int)(c / R);        // CTA holding row gcol
+    const int lrow_c = c - owner_c * R;      // its local index there
+
+    if (!a.chol) {
+      // ---------------- LU: pivot search ------------------------------------
+      uint64_t best = 0;
+      int64_t brow = INT64_MAX;
+      for (int r = tid; r < nrows; r += PT) {
+        int64_t gr = row0 + r;
+        if (gr < gcol) continue;
+        uint64_t k = abs_key(tile[(size_t)r * jb + c]);
+        if (k > best || (k == best && gr < brow)) { best = k; brow = gr; }
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        uint64_t ok = __shfl_down_sync(0xFFFFFFFFu, best, off);
+        int64_t orow = __shfl_down_sync(0xFFFFFFFFu, brow, off);
+        if (ok > best || (ok == best && orow < brow)) { best = ok; brow = orow; }
+      }
+      if ((tid & 31) == 0) { red_key[tid >> 5] = best; red_row[tid >> 5] = brow; }
+      __syncthreads();
+      if (tid == 0) {
+        for (int w = 1; w < PT / 32; ++w)
+          if (red_key[w] > best || (red_key[w] == best && red_row[w] < brow)) {
+            best = red_key[w];
+            brow = red_row[w];
+          }
+        __stcg(&a.cand_key[buf * G + g], best);
+        __stcg(&a.cand_row[buf * G + g], brow);
+        s_piv = brow;
+      }
+      __syncthreads();
+      // the candidate row's panel values, and the current row gcol
+      if (s_piv != INT64_MAX) {
+        int lr = (int)(s_piv - row0);
+        pz *dst = a.cand_vals + ((size_t)buf * G + g) * jb;
+        for (int k = tid; k < jb; k += PT) dst[k] = tile[(size_t)lr * jb + k];
+      }
+      if (g == owner_c) {
+        pz *dst = a.xrow + (size_t)buf * jb;
+        for (int k = tid; k < jb; k += PT) dst[k] = tile[(size_t)lrow_c * jb + k];
+      }
+      if (!grid_barrier(a.bar, G, a.err, a.info)) return;
+
+      // every CTA picks the same pivot: largest |a|, then the lowest row
+      if (tid == 0) {
+        uint64_t bk = 0;
+        int64_t br = INT64_MAX;
+        int bw = 0;
+        for (unsigned w = 0; w < G; ++w) {
+          uint64_t k = __ldcg(&a.cand_key[buf * G + w]);
+          int64_t r = __ldcg(&a.cand_row[buf * G + w]);
+          if (r == INT64_MAX) continue;
+          if (k > bk || (k == bk && r < br)) { bk = k; br = r; bw = (int)w; }
+        }
+        s_piv = br;
+        s_flag = bw;
+      }
+      __syncthreads();
+      const int64_t p = s_piv;
+      const pz *pv = a.cand_vals + ((size_t)buf * G + s_flag) * jb;
+      for (int k = tid; k < jb; k += PT) {
+        pz v;
+        v.s = __ldcg(&pv[k].s);
+        v.m = __ldcg(&pv[k].m);
+        prow[k] = v;
+      }
+      __syncthreads();
+      const bool zero = pz_is_zero(prow[c]);
+      if (!zero && p != gcol) {
+        if (g == owner_c)
+          for (int k = tid; k < jb; k += PT) tile[(size_t)lrow_c * jb + k] = prow[k];
+        if (p >= row0 && p < row0 + nrows) {
+          const pz *old = a.xrow + (size_t)buf * jb;
+          int lr = (int)(p - row0);
+          for (int k = tid; k < jb; k += PT) {
+            pz v;
+            v.s = __ldcg(&old[k].s);
+            v.m = __ldcg(&old[k].m);
+            tile[(size_t)lr * jb + k] = v;
+          }
+        }
+      }
+      if (tid == 0) {
+        if (!zero) s_r = pz_div(pz_one(), prow[c]);
+        if (g == 0) {
+          a.ipiv[gcol] = (int32_t)(p + 1);
+          if (zero && *a.info == 0) *a.info = (int32_t)(gcol + 1);
+        }
+      }
+      __syncthreads();
+      if (!zero) {
+        for (int r = tid; r < nrows; r += PT)
+          if (row0 + r > gcol) tile[(size_t)r * jb + c] = pz_mul(tile[(size_t)r * jb + c], s_r);
+      }
+      __syncthreads();
+      // rank-1 update of the panel columns right of c: a_ik -= l_i * u_k
+      const int ncols = jb - c - 1;
+      if (ncols > 0) {
+        for (int idx = tid; idx < nrows * ncols; idx += PT) {
+          int r = idx / ncols, k = c + 1 + idx % ncols;
+          if (row0 + r <= gcol) continue;
+          pz *x = &tile[(size_t)r * jb + k];
+          *x = pz_sub(*x, pz_mul(tile[(size_t)r * jb + c], prow[k]));
+        }
+      }
+      __syncthreads();
+    } else {
+      // ---------------- Cholesky --------------------------------------------
+      if (tid == 0) {
+        pz d;
+        d.s = __ldcg(&a.diag[buf].s);
+        d.m = __ldcg(&a.diag[buf].m);
+        bool bad = pz_is_nar(d) || pz_is_zero(d) || (d.m >> 31);
+        s_flag = bad;
+        if (bad) {
+          if (g == 0) *a.info = (int32_t)(gcol + 1);
+        } else {
+          pz sq = pz_sqrt(d);
+          s_r = pz_div(pz_one(), sq);
+          prow[0] = sq;
+        }
+      }
+      __syncthreads();
+      if (s_flag) break;  // leave a_jj = d; the tile is written back below
+      if (g == owner_c && tid == 0) tile[(size_t)lrow_c * jb + c] = prow[0];
+      for (int r = tid; r < nrows; r += PT)
+        if (row0 + r > gcol) tile[(size_t)r * jb + c] = pz_mul(tile[(size_t)r * jb + c], s_r);
+      __syncthreads();
+      // broadcast l_{k,c} for the panel rows k in (c, jb) held here
+      {
+        pz *dst = a.xrow + (size_t)buf * jb;
+        for (int r = tid; r < nrows; r += PT) {
+          int64_t kk = row0 + r - a.j;
+          if (kk > c && kk < jb) dst[kk] = tile[(size_t)r * jb + c];
+        }
+      }
+      // the next diagonal element gets its update from column c now, so it
+      // can be published at the same barrier
+      if (c + 1 < jb) {
+        const int owner_n = (int)((c + 1) / R), lrow_n = (c + 1) - owner_n * R;
+        if (g == owner_n && tid == 0) {
+          pz l = tile[(size_t)lrow_n * jb + c];
+          pz *x = &tile[(size_t)lrow_n * jb + c + 1];
+          *x = pz_sub(*x, pz_mul(l, l));
+          a.diag[buf ^ 1] = *x;
+        }
+      }
+      if (!grid_barrier(a.bar, G, a.err, a.info)) return;
+      const int ncols = jb - c - 1;
+      if (ncols > 0) {
+        const pz *src = a.xrow + (size_t)buf * jb;
+        for (int k = c + 1 + tid; k < jb; k += PT) {
+          pz v;
+          v.s = __ldcg(&src[k].s);
+          v.m = __ldcg(&src[k].m);
+          prow[k] = v;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < nrows * ncols; idx += PT) {
+          int r = idx / ncols, k = c + 1 + idx % ncols;
+          int64_t gr = row0 + r;
+          if (gr <= gcol || a.j + k > gr) continue;           // lower triangle only
+          if (gr == a.j + c + 1 && k == c + 1) continue;      // done before the barrier
+          pz *x = &tile[(size_t)r * jb + k];
+          *x = pz_sub(*x, pz_mul(tile[(size_t)r * jb + c], prow[k]));
+        }
+      }
+      __syncthreads();
+    }
+  }
+
+  // write the panel back
+  for (int idx = tid; idx < R * jb; idx += PT) {
+    int r, c;
+    if (a.trans) { c = idx % jb; r = idx / jb; } else { r = idx % R; c = idx / R; }
+    if (r >= nrows) continue;
+    int64_t gr = row0 + r, gc = a.j + c;
+    if (a.chol && gc > gr) continue;  // never touch the other triangle
+    a.A[panel_addr(a, gr, gc)] = pz_to_bits(tile[(size_t)r * jb + c]);
+  }
+}
+
+// The panel's row swaps (pivots k0 .. k1-1) applied to columns [c0, c1).
+__global__ void laswp_kernel(uint32_t *__restrict__ A, int64_t lda, int64_t c0, int64_t c1,
+                             int64_t k0, int64_t k1, const int32_t *__restrict__ ipiv) {
+  for (int64_t col = c0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; col < c1;
+       col += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t *cp = A + col * lda;
+    for (int64_t k = k0; k < k1; ++k) {
+      int64_t p = ipiv[k] - 1;
+      if (p != k) {
+        uint32_t t = cp[k];
+        cp[k] = cp[p];
+        cp[p] = t;
+      }
+    }
+  }
+}
+
+// U12 <- L11^-1 A12 with L11 unit lower (jb x jb at (j, j)), A12 = rows
+// [j, j+jb) of columns [c0, c1).  Element (r, col) of U12 receives
+// l_{r,t} * u_{t,col} for t = 0 .. r-1 in ascending order.
+__global__ void __launch_bounds__(TRSM_T)
+trsm_llu_kernel(uint32_t *__restrict__ A, int64_t lda, int64_t j, int jb, int64_t c0, int64_t c1) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  pz *X = reinterpret_cast<pz *>(smem_raw);   // [jb][TRSM_NC]
+  pz *Lc = X + (size_t)jb * TRSM_NC;          // [jb]
+  const int tid = threadIdx.x;
+  const int64_t cb = c0 + (int64_t)blockIdx.x * TRSM_NC;
+  const int nc = (int)min64(TRSM_NC, c1 - cb);
+  for (int idx = tid; idx < jb * TRSM_NC; idx += TRSM_T) {
+    int r = idx % jb, cc = idx / jb;
+    X[(size_t)r * TRSM_NC + cc] = cc < nc ? pz_decode(A[(j + r) + (cb + cc) * lda]) : pz_zero();
+  }
+  for (int t = 0; t + 1 < jb; ++t) {
+    for (int r = t + 1 + tid; r < jb; r += TRSM_T) Lc[r] = pz_decode(A[(j + r) + (j + t) * lda]);
+    __syncthreads();
+    const int nr = jb - t - 1;
+    for (int idx = tid; idx < nr * TRSM_NC; idx += TRSM_T) {
+      int r = t + 1 + idx / TRSM_NC, cc = idx % TRSM_NC;
+      if (cc >= nc) continue;
+      pz *x = &X[(size_t)r * TRSM_NC + cc];
+      *x = pz_sub(*x, pz_mul(Lc[r], X[(size_t)t * TRSM_NC + cc]));
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < jb * TRSM_NC; idx += TRSM_T) {
+    int r = idx % jb, cc = idx / jb;
+    if (cc < nc) A[(j + r) + (cb + cc) * lda] = pz_to_bits(X[(size_t)r * TRSM_NC + cc]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+struct Scratch {
+  void *base = nullptr;
+  unsigned *bar;
+  int *err;
+  uint64_t *cand_key;
+  int64_t *cand_row;
+  pz *cand_vals;
+  pz *xrow;
+  pz *diag;
+  size_t bytes = 0;
+};
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t scratch_bytes(int Gmax, int jbmax) {
+  return align_up(4 * sizeof(unsigned)) + align_up(2 * (size_t)Gmax * 8) +
+         align_up(2 * (size_t)Gmax * 8) + align_up(2 * (size_t)Gmax * jbmax * sizeof(pz)) +
+         align_up(2 * (size_t)jbmax * sizeof(pz)) + align_up(2 * sizeof(pz));
+}
+
+// Carve the scratch pointers out of one block of `bytes` (see scratch_bytes).
+void carve(Scratch &s, void *base, int Gmax, int jbmax) {
+  char *p = static_cast<char *>(base);
+  s.base = base;
+  s.bar = reinterpret_cast<unsigned *>(p);
+  s.err = reinterpret_cast<int *>(p + 2 * sizeof(unsigned));
+  p += align_up(4 * sizeof(unsigned));
+  s.cand_key = reinterpret_cast<uint64_t *>(p);
+  p += align_up(2 * (size_t)Gmax * 8);
+  s.cand_row = reinterpret_cast<int64_t *>(p);
+  p += align_up(2 * (size_t)Gmax * 8);
+  s.cand_vals = reinterpret_cast<pz *>(p);
+  p += align_up(2 * (size_t)Gmax * jbmax * sizeof(pz));
+  s.xrow = reinterpret_cast<pz *>(p);
+  p += align_up(2 * (size_t)jbmax * sizeof(pz));
+  s.diag = reinterpret_cast<pz *>(p);
+}
+
+struct DeviceLimits {
+  int sms = 0;
+  int smem_optin = 0;
+};
+
+int device_limits(DeviceLimits &d) {
+  int dev;
+  if (cudaGetDevice(&dev) != cudaSuccess) return POSIT_ERR_DEVICE;
+  if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return POSIT_ERR_DEVICE;
+  if (cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+      cudaSuccess)
+    return POSIT_ERR_DEVICE;
+  return POSIT_OK;
+}
+
+constexpr int kNB = 256;        // panel width of the timed path
+constexpr int kMinRows = 32;    // fewest panel rows per CTA worth a CTA
+
+// Shape of one panel launch: G CTAs of R rows, width jb.
+struct PanelShape {
+  int G, R, jb;
+  size_t smem;
+};
+
+PanelShape panel_shape(const DeviceLimits &d, int64_t rows, int jb_want) {
+  PanelShape s;
+  int64_t G = min64(d.sms, max64(1, ceil_div(rows, kMinRows)));
+  int64_t R = ceil_div(rows, G);
+  int jb = jb_want;
+  // shared memory: R x jb tile + one row, decoded (8 bytes per element)
+  size_t cap = (size_t)d.smem_optin - 1024;
+  while (jb > 8 && ((size_t)R * jb + jb) * sizeof(pz) > cap) jb -= 8;
+  s.G = (int)G;
+  s.R = (int)R;
+  s.jb = jb;
+  s.smem = ((size_t)R * jb + jb) * sizeof(pz);
+  return s;
+}
+
+int launch_panel(PanelArgs &pa, const PanelShape &ps, cudaStream_t stream) {
+  if (cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)ps.smem) != cudaSuccess)
+    return POSIT_ERR_CUDA;
+  pa.jb = ps.jb;
+  pa.R = ps.R;
+  void *args[] = {&pa};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void *)panel_kernel, dim3(ps.G), dim3(PT),
+                                              args, ps.smem, stream);
+  return e == cudaSuccess ? POSIT_OK : POSIT_ERR_CUDA;
+}
+
+int trsm_llu(uint32_t *A, int64_t lda, int64_t j, int jb, int64_t c0, int64_t c1,
+             cudaStream_t stream) {
+  if (c1 <= c0 || jb <= 1) return POSIT_OK;
+  size_t smem = ((size_t)jb * TRSM_NC + jb) * sizeof(pz);
+  if (cudaFuncSetAttribute(trsm_llu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
+    return POSIT_ERR_CUDA;
+  dim3 grid((unsigned)ceil_div(c1 - c0, TRSM_NC));
+  trsm_llu_kernel<<<grid, TRSM_T, smem, stream>>>(A, lda, j, jb, c0, c1);
+  return launch_status();
+}
+
+int laswp(uint32_t *A, int64_t lda, int64_t c0, int64_t c1, int64_t k0, int64_t k1,
+          const int32_t *ipiv, cudaStream_t stream) {
+  if (c1 <= c0 || k1 <= k0) return POSIT_OK;
+  int64_t blocks = min64(ceil_div(c1 - c0, 128), 152 * 8);
+  laswp_kernel<<<(unsigned)blocks, 128, 0, stream>>>(A, lda, c0, c1, k0, k1, ipiv);
+  return launch_status();
+}
+
+}  // namespace
+
+// Blocked LU on a caller-provided scratch block (bytes from getrf_scratch_bytes).
+int getrf_run(int64_t m, int64_t n, uint32_t *A, int64_t lda, int32_t *ipiv, int32_t *info,
+              void *scratch, cudaStream_t stream) {
+  DeviceLimits d;
+  int st = device_limits(d);
+  if (st) return st;
+  const int64_t mn = min64(m, n);
+  Scratch s;
+  carve(s, scratch, d.sms, kNB);
+  if (cudaMemsetAsync(scratch, 0, scratch_bytes(d.sms, kNB), stream) != cudaSuccess)
+    return POSIT_ERR_CUDA;
+  for (int64_t j = 0; j < mn;) {
+    PanelShape ps = panel_shape(d, m - j, (int)min64(kNB, mn - j));
+    const int jb = ps.jb;
+    PanelArgs pa{};
+    pa.A = A; pa.lda = lda; pa.m = m; pa.j = j; pa.trans = 0; pa.chol = 0;
+    pa.ipiv = ipiv; pa.info = info;
+    pa.bar = s.bar; pa.err = s.err; pa.cand_key = s.cand_key; pa.cand_row = s.cand_row;
+    pa.cand_vals = s.cand_vals; pa.xrow = s.xrow; pa.diag = s.diag;
+    if ((st = launch_panel(pa, ps, stream))) return st;
+    if ((st = laswp(A, lda, 0, j, j, j + jb, ipiv, stream))) return st;
+    if ((st = laswp(A, lda, j + jb, n, j, j + jb, ipiv, stream))) return st;
+    if (j + jb < n) {
+      if ((st = trsm_llu(A, lda, j, jb, j + jb, n, stream))) return st;
+      if (j + jb < m) {
+        st = rgemm_launch(false, false, TRI_FULL, m - j - jb, n - j - jb, jb, 0xC0000000u,
+                          A + (j + jb) + j * lda, lda, A + j + (j + jb) * lda, lda,
+                          PZ_ONE_BITS, A + (j + jb) + (j + jb) * lda, lda, stream);
+        if (st) return st;
+      }
+    }
+    j += jb;
+  }
+  return POSIT_OK;
+}
+
+size_t getrf_scratch_bytes() {
+  DeviceLimits d;
+  if (device_limits(d)) return 0;
+  return scratch_bytes(d.sms, kNB);
+}
+
+int potrf_run(bool upper, int64_t n, uint32_t *A, int64_t lda, int32_t *info, void *scratch,
+              cudaStream_t stream) {
+  DeviceLimits d;
+  int st = device_limits(d);
+  if (st) return st;
+  Scratch s;
+  carve(s, scratch, d.sms, kNB);
+  if (cudaMemsetAsync(scratch, 0, scratch_bytes(d.sms, kNB), stream) != cudaSuccess)
+    return POSIT_ERR_CUDA;
+  for (int64_t j = 0; j < n;) {
+    PanelShape ps = panel_shape(d, n - j, (int)min64(kNB, n - j));
+    const int jb = ps.jb;
+    PanelArgs pa{};
+    pa.A = A; pa.lda = lda; pa.m = n; pa.j = j; pa.trans = upper ? 1 : 0; pa.chol = 1;
+    pa.ipiv = nullptr; pa.info = info;
+    pa.bar = s.bar; pa.err = s.err; pa.cand_key = s.cand_key; pa.cand_row = s.cand_row;
+    pa.cand_vals = s.cand_vals; pa.xrow = s.xrow; pa.diag = s.diag;
+    if ((st = launch_panel(pa, ps, stream))) return st;
+    if (j + jb < n) {
+      const int64_t t0 = j + jb, nt = n - t0;
+      if (!upper)
+        st = rgemm_launch_guarded(false, true, TRI_LOWER, nt, nt, jb, 0xC0000000u,
+                                  A + t0 + j * lda, lda, A + t0 + j * lda, lda, PZ_ONE_BITS,
+                                  A + t0 + t0 * lda, lda, info, stream);
+      else
+        st = rgemm_launch_guarded(true, false, TRI_UPPER, nt, nt, jb, 0xC0000000u,
+                                  A + j + t0 * lda, lda, A + j + t0 * lda, lda, PZ_ONE_BITS,
+                                  A + t0 + t0 * lda, lda, info, stream);
+      if (st) return st;
+    }
+    j += jb;
+  }
+  return POSIT_OK;
+}
+
+size_t potrf_scratch_bytes() { return getrf_scratch_bytes(); }
+
+}  // namespace posit
+
+using namespace posit;
+
+namespace {
+int with_scratch(size_t bytes, cudaStream_t stream, void **out) {
+  if (cudaMallocAsync(out, bytes, stream) != cudaSuccess) {
+    cudaGetLastError();
+    return POSIT_ERR_ALLOC;
+  }
+  return POSIT_OK;
+}
+}  // namespace
+
+extern "C" int posit_rgetrf(int64_t m, int64_t n, posit32_t *A, int64_t lda, int32_t *ipiv,
+                            int32_t *info, cudaStream_t stream) {
+  if (m < 0) return -1;
+  if (n < 0) return -2;
+  if (lda < max64(1, m)) return -4;
+  if (!info) return -6;
+  if (m > 0 && n > 0 && !A) return -3;
+  if (m > 0 && n > 0 && !ipiv) return -5;
+  if (cudaMemsetAsync(info, 0, sizeof(int32_t), stream) != cudaSuccess) return POSIT_ERR_CUDA;
+  if (m == 0 || n == 0) return POSIT_OK;
+  size_t bytes = getrf_scratch_bytes();
+  if (!bytes) return POSIT_ERR_DEVICE;
+  void *scratch = nullptr;
+  int st = with_scratch(bytes, stream, &scratch);
+  if (st) return st;
+  st = getrf_run(m, n, A, lda, ipiv, info, scratch, stream);
+  cudaFreeAsync(scratch, stream);
+  return st;
+}
+
+extern "C" int posit_rpotrf(char uplo, int64_t n, posit32_t *A, int64_t lda, int32_t *info,
+                            cudaStream_t stream) {
+  if (!is_lower(uplo) && !is_upper(uplo)) return -1;
+  if (n < 0) return -2;
+  if (lda < max64(1, n)) return -4;
+  if (!info) return -5;
+  if (n > 0 && !A) return -3;
+  if (cudaMemsetAsync(info, 0, sizeof(int32_t), stream) != cudaSuccess) return POSIT_ERR_CUDA;
+  if (n == 0) return POSIT_OK;
+  size_t bytes = potrf_scratch_bytes();
+  if (!bytes) return POSIT_ERR_DEVICE;
+  void *scratch = nullptr;
+  int st = with_scratch(bytes, stream, &scratch);
+  if (st) return st;
+  st = potrf_run(is_upper(uplo), n, A, lda, info, scratch, stream);
+  cudaFreeAsync(scratch, stream);
+  return st;
+}

@@ -32,4 +32,26 @@ int rgemm_launch(bool ta, bool tb, int tri, int64_t m, int64_t n, int64_t k,
                  const uint32_t *B, int64_t ldb, uint32_t beta, uint32_t *C,
                  int64_t ldc, cudaStream_t stream);
 
+// Same, skipped by the kernel when *abort_flag != 0 (read on the device).
+int rgemm_launch_guarded(bool ta, bool tb, int tri, int64_t m, int64_t n, int64_t k,
+                         uint32_t alpha, const uint32_t *A, int64_t lda,
+                         const uint32_t *B, int64_t ldb, uint32_t beta, uint32_t *C,
+                         int64_t ldc, const int32_t *abort_flag, cudaStream_t stream);
+
+// Blocked factorisations on a caller-provided scratch block of
+// getrf_scratch_bytes() / potrf_scratch_bytes() bytes (device memory).
+size_t getrf_scratch_bytes();
+size_t potrf_scratch_bytes();
+int getrf_run(int64_t m, int64_t n, uint32_t *A, int64_t lda, int32_t *ipiv, int32_t *info,
+              void *scratch, cudaStream_t stream);
+int potrf_run(bool upper, int64_t n, uint32_t *A, int64_t lda, int32_t *info, void *scratch,
+              cudaStream_t stream);
+
+// Solves on a caller-provided scratch block of solve_scratch_bytes() bytes.
+size_t solve_scratch_bytes();
+int getrs_run(bool trans, int64_t n, int64_t nrhs, const uint32_t *A, int64_t lda,
+              const int32_t *ipiv, uint32_t *B, int64_t ldb, void *scratch, cudaStream_t stream);
+int potrs_run(bool upper, int64_t n, int64_t nrhs, const uint32_t *A, int64_t lda, uint32_t *B,
+              int64_t ldb, void *scratch, cudaStream_t stream);
+
 }  // namespace posit

@@ -12,10 +12,13 @@
 // pre-/post-processing: operate in an internal format, re-encode the regime,
 // round with the new f_s).  Rounding rule (the paper gives none): round the
 // value's posit bit string to 31 bits after the sign, to nearest, ties to the
-// even pattern, saturating at minpos/maxpos.  For |S| <= 111 every exponent
-// bit fits, and this is ordinary round-to-nearest-even of the significand to
-// f_s = 28 - m fraction bits (m = regime run length); that is the fast path.
-// Values with |S| >= 112 use the bit-string encoder (pz_encode).
+// even pattern, saturating at minpos/maxpos.  While the regime run m is at
+// most 27 (-108 <= S <= 107) both exponent bits and at least one fraction bit
+// fit, the last bit of the pattern is a fraction bit, and this is ordinary
+// round-to-nearest-even of the significand to f_s = 28 - m fraction bits; that
+// is the fast path.  From m = 28 on the last bit of the pattern is an
+// exponent bit (or a regime bit), which decides ties, so those scales use the
+// bit-string encoder (pz_encode).
 //
 // Intermediate significands carry a "jam" bit: bit 0 is set when nonzero bits
 // were shifted out below it.  Rounding never keeps more than 28 bits of a
@@ -95,7 +98,7 @@ static __device__ __forceinline__ uint32_t pz_to_bits(pz a) {
   return pz_encode(a.m & 0x80000000u, a.s, a.m & 0x7FFFFFFFu);
 }
 
-// Slow rounding for scales in the exponent-truncated band |S| >= 112.
+// Slow rounding for regimes of 28 or more bits (S <= -109 or S >= 108).
 static __device__ __noinline__ pz pz_round_band(uint32_t sign, int S, uint32_t X) {
   return pz_decode(pz_encode(sign, S, X));
 }
@@ -105,8 +108,8 @@ static __device__ __noinline__ pz pz_round_band(uint32_t sign, int S, uint32_t X
 // decoded form.
 static __device__ __forceinline__ pz pz_round(uint32_t sign, int S, uint32_t X) {
   int km = (S >> 2) ^ (S >> 31);  // regime run length m minus 1
-  if ((unsigned)(km - 28) < (1u << 17)) return pz_round_band(sign, S, X);
-  // q = number of bits below the kept ones: 30 - f_s = 2 + m (3..30); the
+  if ((unsigned)(km - 27) < (1u << 17)) return pz_round_band(sign, S, X);
+  // q = number of bits below the kept ones: 30 - f_s = 2 + m (3..29); the
   // zero/NaR sentinels clamp to 30, which leaves X = 0 and X = 2^30 intact
   uint32_t q = min((uint32_t)km + 3u, 30u);
   uint32_t lsb = (X >> q) & 1u;

@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(NT, 2)
 rgemm_kernel(int64_t M, int64_t N, int64_t K, uint32_t alpha,
              const uint32_t *__restrict__ A, int64_t lda,
              const uint32_t *__restrict__ B, int64_t ldb, uint32_t beta,
-             uint32_t *__restrict__ C, int64_t ldc) {
+             uint32_t *__restrict__ C, int64_t ldc, const int32_t *__restrict__ abort_flag) {
   __shared__ __align__(16) pz As[BK][BM];
   __shared__ __align__(16) pz Bs[BK][BN];
 
@@ -47,6 +47,7 @@ rgemm_kernel(int64_t M, int64_t N, int64_t K, uint32_t alpha,
   const int64_t n0 = (int64_t)blockIdx.y * BN;
   if (TRI == TRI_LOWER && n0 > m0 + BM - 1) return;  // tile wholly above diagonal
   if (TRI == TRI_UPPER && m0 > n0 + BN - 1) return;  // tile wholly below diagonal
+  if (abort_flag != nullptr && *abort_flag != 0) return;  // a factorisation failed
 
   const pz alpha_d = pz_decode(alpha);
   const pz beta_d = pz_decode(beta);
@@ -129,7 +130,8 @@ rgemm_kernel(int64_t M, int64_t N, int64_t K, uint32_t alpha,
 template <int TRI>
 int launch_tri(bool ta, bool tb, int64_t m, int64_t n, int64_t k, uint32_t alpha,
                const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb,
-               uint32_t beta, uint32_t *C, int64_t ldc, cudaStream_t stream) {
+               uint32_t beta, uint32_t *C, int64_t ldc, const int32_t *abort_flag,
+               cudaStream_t stream) {
   const int64_t gx = ceil_div(m, BM);
   // gridDim.y is limited to 65535: split very wide C into column chunks
   const int64_t max_cols = (int64_t)65535 * BN;
@@ -141,13 +143,13 @@ int launch_tri(bool ta, bool tb, int64_t m, int64_t n, int64_t k, uint32_t alpha
     // a column chunk of a triangular update keeps its global diagonal: the
     // chunked path is only used for TRI_FULL (n <= 4M columns otherwise)
     if (!ta && !tb)
-      rgemm_kernel<false, false, TRI><<<grid, NT, 0, stream>>>(m, nc, k, alpha, A, lda, Bp, ldb, beta, Cp, ldc);
+      rgemm_kernel<false, false, TRI><<<grid, NT, 0, stream>>>(m, nc, k, alpha, A, lda, Bp, ldb, beta, Cp, ldc, abort_flag);
     else if (!ta && tb)
-      rgemm_kernel<false, true, TRI><<<grid, NT, 0, stream>>>(m, nc, k, alpha, A, lda, Bp, ldb, beta, Cp, ldc);
+      rgemm_kernel<false, true, TRI><<<grid, NT, 0, stream>>>(m, nc, k, alpha, A, lda, Bp, ldb, beta, Cp, ldc, abort_flag);
     else if (ta && !tb)
-      rgemm_kernel<true, false, TRI><<<grid, NT, 0, stream>>>(m, nc, k, alpha, A, lda, Bp, ldb, beta, Cp, ldc);
+      rgemm_kernel<true, false, TRI><<<grid, NT, 0, stream>>>(m, nc, k, alpha, A, lda, Bp, ldb, beta, Cp, ldc, abort_flag);
     else
-      rgemm_kernel<true, true, TRI><<<grid, NT, 0, stream>>>(m, nc, k, alpha, A, lda, Bp, ldb, beta, Cp, ldc);
+      rgemm_kernel<true, true, TRI><<<grid, NT, 0, stream>>>(m, nc, k, alpha, A, lda, Bp, ldb, beta, Cp, ldc, abort_flag);
     int st = launch_status();
     if (st != POSIT_OK) return st;
   }
@@ -156,16 +158,24 @@ int launch_tri(bool ta, bool tb, int64_t m, int64_t n, int64_t k, uint32_t alpha
 
 }  // namespace
 
+int rgemm_launch_guarded(bool ta, bool tb, int tri, int64_t m, int64_t n, int64_t k,
+                         uint32_t alpha, const uint32_t *A, int64_t lda, const uint32_t *B,
+                         int64_t ldb, uint32_t beta, uint32_t *C, int64_t ldc,
+                         const int32_t *abort_flag, cudaStream_t stream) {
+  if (m <= 0 || n <= 0) return POSIT_OK;
+  if (tri == TRI_LOWER)
+    return launch_tri<TRI_LOWER>(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, abort_flag, stream);
+  if (tri == TRI_UPPER)
+    return launch_tri<TRI_UPPER>(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, abort_flag, stream);
+  return launch_tri<TRI_FULL>(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, abort_flag, stream);
+}
+
 int rgemm_launch(bool ta, bool tb, int tri, int64_t m, int64_t n, int64_t k,
                  uint32_t alpha, const uint32_t *A, int64_t lda, const uint32_t *B,
                  int64_t ldb, uint32_t beta, uint32_t *C, int64_t ldc,
                  cudaStream_t stream) {
-  if (m <= 0 || n <= 0) return POSIT_OK;
-  if (tri == TRI_LOWER)
-    return launch_tri<TRI_LOWER>(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream);
-  if (tri == TRI_UPPER)
-    return launch_tri<TRI_UPPER>(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream);
-  return launch_tri<TRI_FULL>(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream);
+  return rgemm_launch_guarded(ta, tb, tri, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
+                              nullptr, stream);
 }
 
 }  // namespace posit

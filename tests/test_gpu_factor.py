@@ -1,0 +1,287 @@
+"""GPU parity of posit_rgetrf / posit_rpotrf / posit_rgetrs / posit_rpotrs
+against the CPU oracle, word for word (factors, pivots, info, solutions).
+
+Up to n = 2048 the whole factorisation is compared with the oracle's
+unblocked algorithm.  At n = 8192 the factors are checked element by element
+on a sample: every sampled output must equal what its defining recurrence
+gives (in the oracle's arithmetic) from the original matrix and the other
+factor entries it depends on, and sampled pivot steps must pick the largest
+|a|.  If every element passed, the factors would equal the oracle's by
+induction over the operation order."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2401_14117_gb300 import binding, inputs
+from tests.gpu_util import DEV, from_dev, to_dev
+
+pytestmark = pytest.mark.gpu
+
+ONE, MONE = 0x40000000, 0xC0000000
+
+
+def words(shape, seed):
+    return oracle.from_double_array(inputs.uniform(shape, seed))
+
+
+def spd_words(n, seed):
+    return oracle.from_double_array(inputs.spd(n, seed, device=DEV if n > 512 else None))
+
+
+def gpu_getrf(A):
+    m, n = A.shape
+    dA = to_dev(A)
+    ipiv = torch.zeros(max(1, min(m, n)), dtype=torch.int32, device=DEV)
+    info = torch.full((1,), -7, dtype=torch.int32, device=DEV)
+    binding.posit_rgetrf(m, n, dA, m, ipiv, info)
+    torch.cuda.synchronize()
+    return from_dev(dA), ipiv.cpu().numpy()[: min(m, n)], int(info.item())
+
+
+def gpu_potrf(A, uplo="L"):
+    n = A.shape[0]
+    dA = to_dev(A)
+    info = torch.full((1,), -7, dtype=torch.int32, device=DEV)
+    binding.posit_rpotrf(uplo, n, dA, n, info)
+    torch.cuda.synchronize()
+    return from_dev(dA), int(info.item())
+
+
+def assert_same(got, want, what=""):
+    bad = np.argwhere(np.asarray(got) != np.asarray(want))
+    assert bad.size == 0, f"{what}: {len(bad)} words differ, first at {bad[:3].tolist()}"
+
+
+# ----------------------------------------------------------------- Rgetrf
+@pytest.mark.parametrize("m,n", [(1, 1), (5, 5), (64, 64), (300, 300), (257, 513),
+                                 (600, 230), (230, 600), (700, 700)])
+def test_getrf_matches_oracle(m, n):
+    A = words((m, n), m * 1000 + n)
+    F, ipiv, info = gpu_getrf(A)
+    Fo, ipo, info_o = oracle.rgetrf(A)
+    assert_same(F, Fo, "factors")
+    assert np.array_equal(ipiv, ipo) and info == info_o
+
+
+def test_getrf_zero_column_and_nar():
+    A = words((300, 300), 5)
+    A[:, 7] = 0
+    A[:, 260] = 0
+    F, ipiv, info = gpu_getrf(A)
+    Fo, ipo, info_o = oracle.rgetrf(A)
+    assert info == info_o == 8
+    assert_same(F, Fo, "zero columns")
+    assert np.array_equal(ipiv, ipo)
+    B = words((40, 40), 6)
+    B[10, 0] = 0x80000000
+    F, ipiv, info = gpu_getrf(B)
+    Fo, ipo, info_o = oracle.rgetrf(B)
+    assert_same(F, Fo, "NaR")
+    assert np.array_equal(ipiv, ipo)
+
+
+def test_getrf_integer_ties():
+    """Small-integer matrix: many exactly equal |a| (the pivot tie rule) and
+    exact zeros produced by cancellation."""
+    rng = np.random.default_rng(7)
+    A = oracle.from_double_array(rng.integers(-2, 3, size=(290, 290)).astype(float))
+    F, ipiv, info = gpu_getrf(A)
+    Fo, ipo, info_o = oracle.rgetrf(A)
+    assert_same(F, Fo, "ties")
+    assert np.array_equal(ipiv, ipo) and info == info_o
+
+
+def test_getrf_workload_2048_full():
+    n = 2048
+    A = words((n, n), inputs.SEED_BASE + 2)
+    F, ipiv, info = gpu_getrf(A)
+    Fo, ipo, info_o = oracle.rgetrf(A)
+    assert_same(F, Fo, "2048")
+    assert np.array_equal(ipiv, ipo) and info == info_o == 0
+
+
+def _perm_from_ipiv(ipiv):
+    rows = np.arange(ipiv.size)
+    for i, p in enumerate(ipiv):
+        rows[i], rows[p - 1] = rows[p - 1], rows[i]
+    return rows  # final position i holds original row rows[i]
+
+
+def test_getrf_workload_8192_sampled():
+    n = 8192
+    A = words((n, n), inputs.SEED_BASE + 3)
+    F, ipiv, info = gpu_getrf(A)
+    assert info == 0
+    Ap = A[_perm_from_ipiv(ipiv), :]
+    rng = np.random.default_rng(8192)
+    idx = np.concatenate([[0, n - 1, 4095, 4096], rng.integers(0, n, 60)])
+    kdx = np.concatenate([[0, n - 1, 4096, 4095], rng.integers(0, n, 60)])
+    for i, k in zip(idx, kdx):
+        K = min(i, k)
+        c = oracle.rgemm("N", "N", MONE, F[i:i + 1, :K], F[:K, k:k + 1], ONE, Ap[i:i + 1, k:k + 1])
+        if i > k:
+            r = oracle.div(ONE, int(F[k, k]))
+            c = np.array([[oracle.mul(int(c[0, 0]), r)]], np.uint32)
+        assert int(c[0, 0]) == int(F[i, k]), (i, k)
+    # sampled pivot steps: the row that ends at position k had the largest |a|
+    def absw(w):
+        w = w.astype(np.uint32)
+        return np.where(w >> 31 == 1, (~w + np.uint32(1)).astype(np.uint32), w)
+    for k in (0, 1, 255, 256, 4000, n - 2):
+        vals = oracle.rgemm("N", "N", MONE, F[k:, :k], F[:k, k:k + 1], ONE, Ap[k:, k:k + 1])[:, 0]
+        assert absw(vals[:1])[0] >= absw(vals).max(), k
+        assert int(vals[0]) == int(F[k, k])
+
+
+# ----------------------------------------------------------------- Rpotrf
+@pytest.mark.parametrize("n", [1, 5, 64, 255, 300, 513, 700])
+@pytest.mark.parametrize("uplo", ["L", "U"])
+def test_potrf_matches_oracle(n, uplo):
+    A = spd_words(n, n)
+    F, info = gpu_potrf(A, uplo)
+    Fo, info_o = oracle.rpotrf(A, uplo=uplo)
+    assert info == info_o == 0
+    assert_same(F, Fo, "factor")  # the other triangle is untouched on both
+
+
+@pytest.mark.parametrize("uplo", ["L", "U"])
+def test_potrf_not_positive_definite(uplo):
+    n = 300
+    A = spd_words(n, 3)
+    A[270, 270] = oracle.from_double(-1.0)  # fails in the second panel
+    F, info = gpu_potrf(A, uplo)
+    Fo, info_o = oracle.rpotrf(A, uplo=uplo)
+    assert info == info_o == 271
+    tri = np.tril if uplo == "L" else np.triu
+    cols = slice(0, info - 1)
+    if uplo == "L":
+        assert_same(np.tril(F)[:, cols], np.tril(Fo)[:, cols], "columns before the failure")
+    else:
+        assert_same(np.triu(F)[cols, :], np.triu(Fo)[cols, :], "rows before the failure")
+    A2 = spd_words(40, 4)
+    A2[0, 0] = 0
+    F, info = gpu_potrf(A2, uplo)
+    assert info == 1 and F[0, 0] == 0
+
+
+def test_potrf_workload_2048_full():
+    n = 2048
+    A = spd_words(n, inputs.SEED_BASE + 4)
+    F, info = gpu_potrf(A, "L")
+    Fo, info_o = oracle.rpotrf(A, uplo="L")
+    assert info == info_o == 0
+    assert_same(F, Fo, "2048")
+
+
+def test_potrf_workload_8192_sampled():
+    n = 8192
+    A = spd_words(n, inputs.SEED_BASE + 5)
+    F, info = gpu_potrf(A, "L")
+    assert info == 0
+    assert np.array_equal(np.triu(F, 1), np.triu(A, 1))  # upper triangle untouched
+    rng = np.random.default_rng(88)
+    js = np.concatenate([[0, 1, 255, 256, n - 1], rng.integers(0, n, 60)])
+    for j in js:
+        i = int(rng.integers(j, n))
+        for (r, c) in ((j, j), (i, j)):
+            d = oracle.rgemm("N", "T", MONE, F[r:r + 1, :c], F[c:c + 1, :c], ONE, A[r:r + 1, c:c + 1])
+            d = int(d[0, 0])
+            if r == c:
+                want = oracle.sqrt(d)
+            else:
+                want = oracle.mul(d, oracle.div(ONE, int(F[c, c])))
+            assert want == int(F[r, c]), (r, c)
+
+
+# ----------------------------------------------------------------- solves
+@pytest.mark.parametrize("trans", ["N", "T"])
+@pytest.mark.parametrize("n,nrhs", [(1, 1), (7, 2), (300, 1), (300, 9), (513, 3)])
+def test_getrs_matches_oracle(trans, n, nrhs):
+    A = words((n, n), 10 + n)
+    Fo, ipo, _ = oracle.rgetrf(A)
+    B = words((n, nrhs), 20 + n)
+    want = oracle.rgetrs(Fo, ipo, B, trans=trans)
+    dF, dB = to_dev(Fo), to_dev(B)
+    dp = torch.from_numpy(ipo.astype(np.int32)).to(DEV)
+    binding.posit_rgetrs(trans, n, nrhs, dF, n, dp, dB, n)
+    torch.cuda.synchronize()
+    assert_same(from_dev(dB), want, "getrs")
+
+
+@pytest.mark.parametrize("uplo", ["L", "U"])
+@pytest.mark.parametrize("n,nrhs", [(1, 1), (7, 2), (300, 1), (300, 9), (513, 3)])
+def test_potrs_matches_oracle(uplo, n, nrhs):
+    A = spd_words(n, 30 + n)
+    Fo, _ = oracle.rpotrf(A, uplo=uplo)
+    B = words((n, nrhs), 40 + n)
+    want = oracle.rpotrs(Fo, B, uplo=uplo)
+    dF, dB = to_dev(Fo), to_dev(B)
+    binding.posit_rpotrs(uplo, n, nrhs, dF, n, dB, n)
+    torch.cuda.synchronize()
+    assert_same(from_dev(dB), want, "potrs")
+
+
+def test_solve_workload_2048():
+    """Rgetrs / Rpotrs with 1 RHS, b = A (1/sqrt n) in FP64 (Sec. 5.1), on the
+    oracle's factors of the n = 2048 workload matrices, every word."""
+    n = 2048
+    A64 = inputs.uniform((n, n), inputs.SEED_BASE + 6)
+    A = oracle.from_double_array(A64)
+    b = oracle.from_double_array(inputs.rhs(A64)).reshape(n, 1)
+    Fo, ipo, _ = oracle.rgetrf(A)
+    want = oracle.rgetrs(Fo, ipo, b)
+    dF, dB = to_dev(Fo), to_dev(b)
+    dp = torch.from_numpy(ipo.astype(np.int32)).to(DEV)
+    binding.posit_rgetrs("N", n, 1, dF, n, dp, dB, n)
+    torch.cuda.synchronize()
+    assert_same(from_dev(dB), want, "getrs workload")
+    S64 = inputs.spd(n, inputs.SEED_BASE + 7, device=DEV)
+    S = oracle.from_double_array(S64)
+    bs = oracle.from_double_array(inputs.rhs(S64)).reshape(n, 1)
+    Fs, _ = oracle.rpotrf(S)
+    want = oracle.rpotrs(Fs, bs)
+    dF, dB = to_dev(Fs), to_dev(bs)
+    binding.posit_rpotrs("L", n, 1, dF, n, dB, n)
+    torch.cuda.synchronize()
+    assert_same(from_dev(dB), want, "potrs workload")
+
+
+@pytest.mark.parametrize("kind", ["getrs", "potrs"])
+def test_solve_8192_synthetic_factors(kind):
+    """n = 8192, 1 RHS: the solve alone on seeded factor-shaped matrices
+    (the oracle cannot factor n = 8192 in test time): unit-lower L and upper U
+    (or L with positive diagonal) with uniform entries and a random valid
+    pivot vector."""
+    n = 8192
+    rng = np.random.default_rng(8192)
+    F = words((n, n), inputs.SEED_BASE + 8)
+    d = np.arange(n)
+    F[d, d] = oracle.from_double_array(rng.uniform(1.0, 2.0, n))
+    b = words((n, 1), inputs.SEED_BASE + 9)
+    dF, dB = to_dev(F), to_dev(b)
+    if kind == "getrs":
+        ipiv = (d + rng.integers(0, 16, n)).clip(max=n - 1).astype(np.int32) + 1
+        want = oracle.rgetrs(F, ipiv, b)
+        binding.posit_rgetrs("N", n, 1, dF, n, torch.from_numpy(ipiv).to(DEV), dB, n)
+    else:
+        want = oracle.rpotrs(F, b)
+        binding.posit_rpotrs("L", n, 1, dF, n, dB, n)
+    torch.cuda.synchronize()
+    assert_same(from_dev(dB), want, kind)
+
+
+def test_argument_errors():
+    with pytest.raises(binding.PositError) as e:
+        binding.posit_rgetrf(-1, 1, None, 1, None, None)
+    assert e.value.code == -1
+    with pytest.raises(binding.PositError) as e:
+        binding.posit_rpotrf("X", 1, None, 1, None)
+    assert e.value.code == -1
+    with pytest.raises(binding.PositError) as e:
+        binding.posit_rgetrs("N", 4, 1, None, 2, None, None, 4)
+    assert e.value.code == -5
+    info = torch.zeros(1, dtype=torch.int32, device=DEV)
+    binding.posit_rgetrf(0, 5, None, 1, None, info)
+    binding.posit_rpotrf("L", 0, None, 1, info)
+    assert int(info.item()) == 0
