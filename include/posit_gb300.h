@@ -164,6 +164,66 @@ POSIT_API int posit_rpotrf(char uplo, int64_t n, posit32_t *A, int64_t lda, int3
 POSIT_API int posit_rpotrs(char uplo, int64_t n, int64_t nrhs, const posit32_t *A, int64_t lda,
                  posit32_t *B, int64_t ldb, cudaStream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched factor + solve: many independent problems in one persistent launch
+ * (the batching pattern built on the paper's Rgetrf/Rgetrs and
+ * Rpotrf/Rpotrs, Sec. 5).
+ *
+ * problems: DEVICE array of `count` descriptors.  For each problem:
+ *   kind POSIT_LU:       A (n x n, lda) is overwritten by its LU factors as
+ *                        posit_rgetrf does, ipiv (n int32) receives the
+ *                        pivots, B (n x nrhs, ldb) is overwritten by the
+ *                        solution of A X = B as posit_rgetrs('N') gives it;
+ *   kind POSIT_CHOLESKY: the lower triangle of A is overwritten by L as
+ *                        posit_rpotrf('L') does and B by the posit_rpotrs('L')
+ *                        solution (B is left unchanged if info > 0).
+ * *info (device int32, may be NULL) receives the factorisation's info.
+ * Every output word equals the corresponding single-problem routine's.
+ * order: optional DEVICE array (count int32): the problems are started in
+ * this order (e.g. largest n first); NULL means 0, 1, 2, ...
+ * max_n, max_nrhs: upper bounds over the problems (size the workspace).
+ * plan: launch shape (any valid plan gives the same results):
+ *   threads      threads per CTA (multiple of 32, <= 1024)
+ *   ctas_per_sm  persistent CTAs per SM
+ *   smem_bytes   shared memory per CTA; a problem whose n*n + 2*n*nrhs
+ *                decoded elements (8 bytes each) fit is kept there,
+ *                others use the CTA's slice of the workspace.
+ * workspace: DEVICE memory of posit_batched_workspace_size() bytes, or NULL
+ * to allocate it stream-ordered inside the call.  With a workspace the call
+ * performs no allocation and enqueues one memset and one kernel.
+ * Errors: -1 count, -2 problems NULL, -4 max_n, -5 max_nrhs, -6 plan.
+ * ------------------------------------------------------------------------ */
+#define POSIT_LU 0
+#define POSIT_CHOLESKY 1
+
+typedef struct posit_problem {
+  int32_t kind;      /* POSIT_LU or POSIT_CHOLESKY */
+  int32_t n;
+  int32_t nrhs;
+  int32_t reserved;
+  int64_t lda;
+  int64_t ldb;
+  posit32_t *A;
+  posit32_t *B;
+  int32_t *ipiv;     /* LU only */
+  int32_t *info;
+} posit_problem;
+
+typedef struct posit_plan {
+  int32_t threads;
+  int32_t ctas_per_sm;
+  int32_t smem_bytes;
+  int32_t reserved;
+} posit_plan;
+
+POSIT_API int posit_batched_workspace_size(int64_t max_n, int64_t max_nrhs,
+                                           const posit_plan *plan, size_t *bytes);
+
+POSIT_API int posit_factor_solve_batched(int64_t count, const posit_problem *problems,
+                                         const int32_t *order, int64_t max_n, int64_t max_nrhs,
+                                         const posit_plan *plan, void *workspace,
+                                         cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

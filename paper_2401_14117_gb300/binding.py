@@ -36,7 +36,24 @@ _SIGS = {
     "posit_rgetrs": [c_char, c_i64, c_i64, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp],
     "posit_rpotrf": [c_char, c_i64, c_vp, c_i64, c_vp, c_vp],
     "posit_rpotrs": [c_char, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp],
+    "posit_batched_workspace_size": [c_i64, c_i64, c_vp, c_vp],
+    "posit_factor_solve_batched": [c_i64, c_vp, c_vp, c_i64, c_i64, c_vp, c_vp, c_vp],
 }
+
+POSIT_LU = 0
+POSIT_CHOLESKY = 1
+
+
+class posit_plan(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("smem_bytes", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+# layout of struct posit_problem (include/posit_gb300.h), for building the
+# device descriptor array from numpy
+PROBLEM_DTYPE = [("kind", "<i4"), ("n", "<i4"), ("nrhs", "<i4"), ("reserved", "<i4"),
+                 ("lda", "<i8"), ("ldb", "<i8"), ("A", "<u8"), ("B", "<u8"),
+                 ("ipiv", "<u8"), ("info", "<u8")]
 
 
 class PositError(RuntimeError):
@@ -140,3 +157,17 @@ def posit_rpotrf(uplo, n, A, lda, info, stream=None):
 def posit_rpotrs(uplo, n, nrhs, A, lda, B, ldb, stream=None):
     return _check("posit_rpotrs", lib().posit_rpotrs(_char(uplo), n, nrhs, _ptr(A), lda,
                                                       _ptr(B), ldb, _stream(stream)))
+
+
+def posit_batched_workspace_size(max_n, max_nrhs, plan):
+    out = ctypes.c_size_t(0)
+    _check("posit_batched_workspace_size", lib().posit_batched_workspace_size(
+        max_n, max_nrhs, ctypes.byref(plan), ctypes.byref(out)))
+    return out.value
+
+
+def posit_factor_solve_batched(count, problems, order, max_n, max_nrhs, plan, workspace,
+                               stream=None):
+    return _check("posit_factor_solve_batched", lib().posit_factor_solve_batched(
+        count, _ptr(problems), _ptr(order), max_n, max_nrhs, ctypes.byref(plan),
+        _ptr(workspace), _stream(stream)))

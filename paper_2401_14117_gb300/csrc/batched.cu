@@ -1,0 +1,325 @@
+// batched.cu -- many independent Rgetrf+Rgetrs / Rpotrf+Rpotrs problems in
+// one persistent launch.
+//
+// A persistent grid of CTAs pulls problem indices from an atomic counter, in
+// the order given by the plan (largest n first, so the longest problems start
+// first).  Each CTA factors and solves one problem at a time, with the matrix
+// decoded (scale, significand pairs) either in shared memory, when n*n*8
+// bytes fit the plan's shared-memory budget, or in the CTA's slice of a
+// global workspace.  The per-element operation order is the unblocked order
+// of Rgetrf/Rpotrf and the trsm orders of Rgetrs/Rpotrs (see
+// include/posit_gb300.h), so every result equals the plain routines' result
+// bit for bit, whatever the plan.
+#include "internal.cuh"
+
+namespace posit {
+namespace {
+
+struct Key {
+  uint64_t k;
+  int r;
+};
+
+__device__ __forceinline__ uint64_t abs_key(pz a) {
+  if (pz_is_nar(a)) return ~0ull;
+  if (pz_is_zero(a)) return 1ull;
+  return ((uint64_t)(uint32_t)(a.s + (1 << 24)) << 32) | (uint64_t)(a.m & 0x7FFFFFFFu);
+}
+
+__device__ __forceinline__ bool key_better(uint64_t k1, int r1, uint64_t k2, int r2) {
+  return k1 > k2 || (k1 == k2 && r1 < r2);
+}
+
+// Block-wide argmax of (key, lowest row); returns the winner in every thread.
+__device__ Key block_argmax(uint64_t k, int r, Key *red) {
+  for (int off = 16; off > 0; off >>= 1) {
+    uint64_t ok = __shfl_down_sync(0xFFFFFFFFu, k, off);
+    int orow = __shfl_down_sync(0xFFFFFFFFu, r, off);
+    if (key_better(ok, orow, k, r)) { k = ok; r = orow; }
+  }
+  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if ((threadIdx.x & 31) == 0) red[w] = Key{k, r};
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Key b = red[0];
+    for (int i = 1; i < nw; ++i)
+      if (key_better(red[i].k, red[i].r, b.k, b.r)) b = red[i];
+    red[32] = b;
+  }
+  __syncthreads();
+  Key out = red[32];
+  __syncthreads();
+  return out;
+}
+
+// LU with partial pivoting of the decoded n x n matrix M (column-major, ld n).
+__device__ int lu_decoded(pz *M, int n, int32_t *ipiv, Key *red, pz *sh) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  int info = 0;
+  for (int c = 0; c < n; ++c) {
+    uint64_t best = 0;
+    int brow = 0x7FFFFFFF;
+    for (int i = c + tid; i < n; i += nt) {
+      uint64_t k = abs_key(M[i + (size_t)c * n]);
+      if (key_better(k, i, best, brow)) { best = k; brow = i; }
+    }
+    Key w = block_argmax(best, brow, red);
+    const int p = w.r;
+    const bool zero = pz_is_zero(M[p + (size_t)c * n]);
+    if (tid == 0) ipiv[c] = p + 1;
+    if (zero) {
+      if (info == 0) info = c + 1;
+    } else {
+      if (p != c)
+        for (int k = tid; k < n; k += nt) {
+          pz t = M[c + (size_t)k * n];
+          M[c + (size_t)k * n] = M[p + (size_t)k * n];
+          M[p + (size_t)k * n] = t;
+        }
+      __syncthreads();
+      // after the swap the pivot sits at (c, c)
+      if (tid == 0) sh[0] = pz_div(pz_one(), M[c + (size_t)c * n]);
+      __syncthreads();
+      const pz r = sh[0];
+      for (int i = c + 1 + tid; i < n; i += nt) M[i + (size_t)c * n] = pz_mul(M[i + (size_t)c * n], r);
+    }
+    __syncthreads();
+    const int m = n - c - 1;
+    for (int idx = tid; idx < m * m; idx += nt) {
+      int i = c + 1 + idx % m, k = c + 1 + idx / m;
+      pz *x = &M[i + (size_t)k * n];
+      *x = pz_sub(*x, pz_mul(M[i + (size_t)c * n], M[c + (size_t)k * n]));
+    }
+    __syncthreads();
+  }
+  return info;
+}
+
+// Cholesky (lower) of the decoded matrix; returns info.
+__device__ int chol_decoded(pz *M, int n, pz *sh) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int j = 0; j < n; ++j) {
+    pz d = M[j + (size_t)j * n];
+    if (pz_is_nar(d) || pz_is_zero(d) || (d.m >> 31)) return j + 1;
+    if (tid == 0) {
+      pz s = pz_sqrt(d);
+      sh[0] = s;
+      sh[1] = pz_div(pz_one(), s);
+    }
+    __syncthreads();
+    if (tid == 0) M[j + (size_t)j * n] = sh[0];
+    const pz r = sh[1];
+    for (int i = j + 1 + tid; i < n; i += nt) M[i + (size_t)j * n] = pz_mul(M[i + (size_t)j * n], r);
+    __syncthreads();
+    const int m = n - j - 1;
+    for (int idx = tid; idx < m * m; idx += nt) {
+      int i = j + 1 + idx % m, k = j + 1 + idx / m;
+      if (k > i) continue;
+      pz *x = &M[i + (size_t)k * n];
+      *x = pz_sub(*x, pz_mul(M[i + (size_t)j * n], M[k + (size_t)j * n]));
+    }
+    __syncthreads();
+  }
+  return 0;
+}
+
+// Rgetrs 'N' on decoded factors: swaps, L y = b (unit), U x = y.
+__device__ void getrs_decoded(const pz *M, int n, const int32_t *ipiv, pz *X, int nrhs) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int c = tid; c < nrhs; c += nt)
+    for (int i = 0; i < n; ++i) {
+      int p = ipiv[i] - 1;
+      pz t = X[i + c * n];
+      X[i + c * n] = X[p + c * n];
+      X[p + c * n] = t;
+    }
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    const int m = n - j - 1;
+    for (int idx = tid; idx < m * nrhs; idx += nt) {
+      int i = j + 1 + idx % m, c = idx / m;
+      X[i + c * n] = pz_sub(X[i + c * n], pz_mul(M[i + (size_t)j * n], X[j + c * n]));
+    }
+    __syncthreads();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    for (int c = tid; c < nrhs; c += nt) X[k + c * n] = pz_div(X[k + c * n], M[k + (size_t)k * n]);
+    __syncthreads();
+    for (int idx = tid; idx < k * nrhs; idx += nt) {
+      int i = idx % k, c = idx / k;
+      X[i + c * n] = pz_sub(X[i + c * n], pz_mul(M[i + (size_t)k * n], X[k + c * n]));
+    }
+    __syncthreads();
+  }
+}
+
+// Rpotrs 'L' on the decoded factor: L y = b then the dot-form L^T x = y.
+__device__ void potrs_decoded(const pz *M, int n, pz *X, int nrhs, pz *prod) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int j = 0; j < n; ++j) {
+    for (int c = tid; c < nrhs; c += nt) X[j + c * n] = pz_div(X[j + c * n], M[j + (size_t)j * n]);
+    __syncthreads();
+    const int m = n - j - 1;
+    for (int idx = tid; idx < m * nrhs; idx += nt) {
+      int i = j + 1 + idx % m, c = idx / m;
+      X[i + c * n] = pz_sub(X[i + c * n], pz_mul(M[i + (size_t)j * n], X[j + c * n]));
+    }
+    __syncthreads();
+  }
+  // x_i = (y_i - sum_{k>i, ascending} l_ki x_k) / l_ii: products in parallel,
+  // one serial chain of subtractions per right-hand side
+  for (int i = n - 1; i >= 0; --i) {
+    const int m = n - i - 1;
+    for (int idx = tid; idx < m * nrhs; idx += nt) {
+      int k = i + 1 + idx % m, c = idx / m;
+      prod[idx] = pz_mul(M[k + (size_t)i * n], X[k + c * n]);
+    }
+    __syncthreads();
+    for (int c = tid; c < nrhs; c += nt) {
+      pz acc = X[i + c * n];
+      for (int t = 0; t < m; ++t) acc = pz_sub(acc, prod[t + c * m]);
+      X[i + c * n] = pz_div(acc, M[i + (size_t)i * n]);
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void batched_kernel(const posit_problem *__restrict__ probs,
+                               const int32_t *__restrict__ order, int64_t count,
+                               unsigned long long *counter, pz *workspace,
+                               size_t ws_elems_per_cta, int smem_elems) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  pz *sm = reinterpret_cast<pz *>(smem_raw);
+  __shared__ Key red[33];
+  __shared__ pz sh[2];
+  __shared__ long long s_idx;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  pz *ws = workspace + (size_t)blockIdx.x * ws_elems_per_cta;
+  for (;;) {
+    if (tid == 0) {
+      unsigned long long i = atomicAdd(counter, 1ull);
+      s_idx = (long long)i < count ? (long long)i : -1;
+    }
+    __syncthreads();
+    const long long qi = s_idx;
+    __syncthreads();
+    if (qi < 0) break;
+    const posit_problem P = probs[order ? order[qi] : qi];
+    const int n = P.n, nrhs = P.nrhs;
+    const size_t need = (size_t)n * n + (size_t)n * nrhs + (size_t)n * nrhs;
+    pz *M = need <= (size_t)smem_elems ? sm : ws;
+    pz *X = M + (size_t)n * n;
+    pz *prod = X + (size_t)n * nrhs;
+    for (int idx = tid; idx < n * n; idx += nt) {
+      int i = idx % n, k = idx / n;
+      M[idx] = (P.kind == POSIT_CHOLESKY && k > i) ? pz_zero() : pz_decode(P.A[i + (int64_t)k * P.lda]);
+    }
+    for (int idx = tid; idx < n * nrhs; idx += nt) {
+      int i = idx % n, c = idx / n;
+      X[idx] = pz_decode(P.B[i + (int64_t)c * P.ldb]);
+    }
+    __syncthreads();
+    int info;
+    if (P.kind == POSIT_LU) {
+      info = lu_decoded(M, n, P.ipiv, red, sh);
+      getrs_decoded(M, n, P.ipiv, X, nrhs);
+    } else {
+      info = chol_decoded(M, n, sh);
+      if (info == 0) potrs_decoded(M, n, X, nrhs, prod);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < n * n; idx += nt) {
+      int i = idx % n, k = idx / n;
+      if (P.kind == POSIT_CHOLESKY && k > i) continue;
+      P.A[i + (int64_t)k * P.lda] = pz_to_bits(M[idx]);
+    }
+    if (P.kind == POSIT_LU || info == 0)
+      for (int idx = tid; idx < n * nrhs; idx += nt) {
+        int i = idx % n, c = idx / n;
+        P.B[i + (int64_t)c * P.ldb] = pz_to_bits(X[idx]);
+      }
+    if (tid == 0 && P.info) *P.info = info;
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+size_t batched_ws_elems(int max_n, int max_nrhs) {
+  return (size_t)max_n * max_n + 2 * (size_t)max_n * max_nrhs;
+}
+
+int batched_launch(const posit_problem *probs, const int32_t *order, int64_t count, int max_n,
+                   int max_nrhs, const posit_plan &plan, void *workspace, cudaStream_t stream) {
+  int dev, sms;
+  if (cudaGetDevice(&dev) != cudaSuccess) return POSIT_ERR_DEVICE;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return POSIT_ERR_DEVICE;
+  const int grid = sms * plan.ctas_per_sm;
+  unsigned long long *counter = static_cast<unsigned long long *>(workspace);
+  pz *ws = reinterpret_cast<pz *>(static_cast<char *>(workspace) + 256);
+  const size_t per = batched_ws_elems(max_n, max_nrhs);
+  if (cudaMemsetAsync(counter, 0, sizeof(unsigned long long), stream) != cudaSuccess)
+    return POSIT_ERR_CUDA;
+  const size_t smem = (size_t)plan.smem_bytes;
+  if (cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
+    return POSIT_ERR_CUDA;
+  batched_kernel<<<grid, plan.threads, smem, stream>>>(probs, order, count, counter, ws, per,
+                                                       (int)(smem / sizeof(pz)));
+  return launch_status();
+}
+
+size_t batched_workspace_bytes(int max_n, int max_nrhs, const posit_plan &plan) {
+  int dev, sms;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return 256 + (size_t)sms * plan.ctas_per_sm * batched_ws_elems(max_n, max_nrhs) * sizeof(pz);
+}
+
+}  // namespace posit
+
+using namespace posit;
+
+namespace {
+bool plan_ok(const posit_plan *p) {
+  return p && p->threads >= 32 && p->threads <= 1024 && (p->threads % 32) == 0 &&
+         p->ctas_per_sm >= 1 && p->ctas_per_sm <= 32 && p->smem_bytes >= 0 &&
+         p->smem_bytes <= 232448;
+}
+}  // namespace
+
+extern "C" int posit_batched_workspace_size(int64_t max_n, int64_t max_nrhs, const posit_plan *plan,
+                                            size_t *bytes) {
+  if (max_n < 0) return -1;
+  if (max_nrhs < 0) return -2;
+  if (!plan_ok(plan)) return -3;
+  if (!bytes) return -4;
+  *bytes = batched_workspace_bytes((int)max_n, (int)max_nrhs, *plan);
+  return *bytes ? POSIT_OK : POSIT_ERR_DEVICE;
+}
+
+extern "C" int posit_factor_solve_batched(int64_t count, const posit_problem *problems,
+                                          const int32_t *order, int64_t max_n, int64_t max_nrhs,
+                                          const posit_plan *plan, void *workspace,
+                                          cudaStream_t stream) {
+  if (count < 0) return -1;
+  if (count > 0 && !problems) return -2;
+  if (max_n < 0 || max_n > 46340) return -4;
+  if (max_nrhs < 0) return -5;
+  if (!plan_ok(plan)) return -6;
+  if (count == 0) return POSIT_OK;
+  if (!workspace) {
+    size_t bytes = batched_workspace_bytes((int)max_n, (int)max_nrhs, *plan);
+    void *ws = nullptr;
+    if (!bytes) return POSIT_ERR_DEVICE;
+    if (cudaMallocAsync(&ws, bytes, stream) != cudaSuccess) {
+      cudaGetLastError();
+      return POSIT_ERR_ALLOC;
+    }
+    int st = batched_launch(problems, order, count, (int)max_n, (int)max_nrhs, *plan, ws, stream);
+    cudaFreeAsync(ws, stream);
+    return st;
+  }
+  return batched_launch(problems, order, count, (int)max_n, (int)max_nrhs, *plan, workspace, stream);
+}

@@ -76,6 +76,8 @@ __device__ bool grid_barrier(unsigned *bar, unsigned nblocks, int *err, int32_t 
 // is the order of the words' two's-complement absolute values (NaR largest,
 // zero smallest).
 __device__ __forceinline__ uint64_t abs_key(pz a) {
+  if (pz_is_nar(a)) return ~0ull;
+  if (pz_is_zero(a)) return 1ull;  // 0 is kept for "no candidate"
   return ((uint64_t)(uint32_t)(a.s + (1 << 24)) << 32) | (uint64_t)(a.m & 0x7FFFFFFFu);
 }
 

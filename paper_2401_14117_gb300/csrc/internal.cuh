@@ -54,4 +54,9 @@ int getrs_run(bool trans, int64_t n, int64_t nrhs, const uint32_t *A, int64_t ld
 int potrs_run(bool upper, int64_t n, int64_t nrhs, const uint32_t *A, int64_t lda, uint32_t *B,
               int64_t ldb, void *scratch, cudaStream_t stream);
 
+// Batched factor + solve (batched.cu).
+size_t batched_workspace_bytes(int max_n, int max_nrhs, const posit_plan &plan);
+int batched_launch(const posit_problem *probs, const int32_t *order, int64_t count, int max_n,
+                   int max_nrhs, const posit_plan &plan, void *workspace, cudaStream_t stream);
+
 }  // namespace posit

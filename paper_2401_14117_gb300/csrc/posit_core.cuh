@@ -29,6 +29,8 @@
 
 #define PZ_SZERO (-(1 << 20))
 #define PZ_SNAR (1 << 22)
+#define PZ_NAR_T (1 << 21)     // s >= PZ_NAR_T: NaR
+#define PZ_ZERO_T (-(1 << 19)) // s <= PZ_ZERO_T: zero (then m's magnitude is 0)
 #define PZ_NAR_BITS 0x80000000u
 #define PZ_ONE_BITS 0x40000000u
 
@@ -119,6 +121,42 @@ static __device__ __forceinline__ pz pz_round(uint32_t sign, int S, uint32_t X) 
   return pz{S + (int)c, sign | (r >> c)};
 }
 
+// Rounding constants per scale, for kernels that keep a 256-entry table in
+// shared memory (index S + 128).  q = 2 + m bits are dropped below the kept
+// ones (lead at bit 30); scales whose regime has 28 or more bits, and every
+// scale outside [-128, 127] (zero, saturation), are marked q = 255 and take
+// the general path.
+struct __align__(16) pz_rtab {
+  uint32_t keep;  // ~((1 << q) - 1)
+  uint32_t hm1;   // (1 << (q - 1)) - 1
+  uint32_t q;
+  uint32_t pad;
+};
+
+static __device__ __forceinline__ pz_rtab pz_rtab_entry(int i) {
+  int S = i - 128, k = S >> 2, m = k >= 0 ? k + 1 : -k;
+  pz_rtab e;
+  if (m >= 28) {
+    e.keep = 0; e.hm1 = 0; e.q = 255u;
+  } else {
+    uint32_t q = 2u + (uint32_t)m;
+    e.keep = 0xFFFFFFFFu << q; e.hm1 = (1u << (q - 1)) - 1u; e.q = q;
+  }
+  e.pad = 0;
+  return e;
+}
+
+// pz_round with the per-scale constants read from the table.
+static __device__ __forceinline__ pz pz_round_tab(const pz_rtab *tab, uint32_t sign, int S,
+                                                  uint32_t X) {
+  const pz_rtab e = tab[min((unsigned)(S + 128), 255u)];
+  if (e.q > 31u) return pz_round(sign, S, X);
+  uint32_t lsb = (X >> e.q) & 1u;
+  uint32_t r = (X + e.hm1 + lsb) & e.keep;
+  uint32_t c = r >> 31;
+  return pz{S + (int)c, sign | (r >> c)};
+}
+
 // ---------------------------------------------------------------------------
 // arithmetic
 // ---------------------------------------------------------------------------
@@ -128,27 +166,47 @@ static __device__ __forceinline__ pz pz_neg(pz a) {
   return pz{a.s, a.m ^ 0x80000000u};
 }
 
-// a (x) b, one rounding.  The 28x28-bit significand product is exact in 64
-// bits; its leading one lands at bit 61 or 62.
-static __device__ __forceinline__ pz pz_mul(pz a, pz b) {
+// a (x) b, one rounding, for operands that are not NaR (zero is fine: its
+// magnitude 0 gives a zero product whose scale stays far below real ones).
+// The 28x28-bit significand product is exact in 64 bits; its leading one
+// lands at bit 61 or 62.
+// The unrounded product: sign, scale and significand (lead at bit 30, jam).
+static __device__ __forceinline__ void pz_mul_exact(pz a, pz b, uint32_t &sign, int &S,
+                                                    uint32_t &X) {
   uint32_t A = a.m & 0x7FFFFFFFu;  // leading one at bit 30 (or 0)
   uint32_t B = b.m << 1;           // leading one at bit 31 (or 0)
   uint64_t P = (uint64_t)A * (uint64_t)B;
   uint32_t hi = (uint32_t)(P >> 32), lo = (uint32_t)P;
   uint32_t t = hi >> 30;           // 1 if the leading one is at bit 62
-  uint32_t sh = 1u - t;
-  uint32_t X = __funnelshift_l(lo, hi, sh);  // leading one to bit 30
-  uint32_t rest = lo << sh;
-  X |= min(rest, 1u);              // jam
-  int S = a.s + b.s + (int)t;
-  return pz_round((a.m ^ b.m) & 0x80000000u, S, X);
+  // leading one to bit 30; every bit of lo below is jammed into bit 0 (bit 0
+  // is below the guard bit, so the lo bit shifted in needs no special care)
+  X = __funnelshift_l(lo, hi, 1u - t) | min(lo, 1u);
+  S = a.s + b.s + (int)t;
+  sign = (a.m ^ b.m) & 0x80000000u;
 }
 
-// c (+) t, one rounding.  Sign-magnitude add with the smaller-scale operand
-// shifted right by d (capped at 31) and its shifted-out bits jammed into
-// bit 0.  With the larger magnitude's lead at bit 30, a same-sign sum stays
-// below 2^32, and a difference is negative only when d = 0 (then exact).
-static __device__ __forceinline__ pz pz_add(pz c, pz t) {
+static __device__ __forceinline__ pz pz_mul_fast(pz a, pz b) {
+  uint32_t sign, X;
+  int S;
+  pz_mul_exact(a, b, sign, S, X);
+  return pz_round(sign, S, X);
+}
+
+static __device__ __forceinline__ pz pz_mul_tab(const pz_rtab *tab, pz a, pz b) {
+  uint32_t sign, X;
+  int S;
+  pz_mul_exact(a, b, sign, S, X);
+  return pz_round_tab(tab, sign, S, X);
+}
+
+// c (+) t, one rounding, for operands that are not NaR.  Sign-magnitude add
+// with the smaller-scale operand shifted right by d (capped at 31) and its
+// shifted-out bits jammed into bit 0.  With the larger magnitude's lead at
+// bit 30, a same-sign sum stays below 2^32, and a difference is negative only
+// when d = 0 (then exact).
+// The unrounded sum: sign, scale and significand (lead at bit 30, jam).
+static __device__ __forceinline__ void pz_add_exact(pz c, pz t, uint32_t &sign, int &Sout,
+                                                    uint32_t &Xout) {
   bool sw = t.s > c.s;
   int SL = sw ? t.s : c.s;
   int SS = sw ? c.s : t.s;
@@ -164,13 +222,46 @@ static __device__ __forceinline__ pz pz_add(pz c, pz t) {
   uint32_t R = sub ? (magL - shv) : (magL + shv);
   uint32_t neg = sub & (R >> 31);  // difference went negative (d = 0 only)
   R = neg ? (0u - R) : R;
-  uint32_t sign = (mL & 0x80000000u) ^ (neg << 31);
+  uint32_t sgn = (mL & 0x80000000u) ^ (neg << 31);
   int lz = __clz(R);
   int sft = lz - 1;  // left shift putting the leading one at bit 30
   uint32_t X = sft >= 0 ? (R << sft) : ((R >> 1) | (R & 1u));
   int S = SL - sft;
   S = (R == 0u) ? PZ_SZERO : S;  // exact cancellation
+  sign = sgn;
+  Sout = S;
+  Xout = X;
+}
+
+static __device__ __forceinline__ pz pz_add_fast(pz c, pz t) {
+  uint32_t sign, X;
+  int S;
+  pz_add_exact(c, t, sign, S, X);
   return pz_round(sign, S, X);
+}
+
+static __device__ __forceinline__ pz pz_add_tab(const pz_rtab *tab, pz c, pz t) {
+  uint32_t sign, X;
+  int S;
+  pz_add_exact(c, t, sign, S, X);
+  return pz_round_tab(tab, sign, S, X);
+}
+
+// General a (x) b and c (+) t: NaR in, NaR out, and the zero / NaR scales
+// are put back to their canonical values so that chains of operations never
+// drift between the two ranges.
+static __device__ __forceinline__ pz pz_canon(pz r, bool nar) {
+  if (nar || r.s >= PZ_NAR_T) return pz_nar();
+  if (r.s <= PZ_ZERO_T) return pz_zero();
+  return r;
+}
+
+static __device__ __forceinline__ pz pz_mul(pz a, pz b) {
+  return pz_canon(pz_mul_fast(a, b), pz_is_nar(a) || pz_is_nar(b));
+}
+
+static __device__ __forceinline__ pz pz_add(pz c, pz t) {
+  return pz_canon(pz_add_fast(c, t), pz_is_nar(c) || pz_is_nar(t));
 }
 
 static __device__ __forceinline__ pz pz_sub(pz c, pz t) { return pz_add(c, pz_neg(t)); }

@@ -11,19 +11,30 @@
 //     tile is pre-multiplied by alpha (t = alpha * op(B)_lj, one rounding);
 //   * each thread owns a TM x TN register tile of C, kept DECODED across the
 //     whole k loop, and applies c = c + t * a for l ascending -- TM*TN
-//     independent dependency chains per thread give the instruction-level
-//     parallelism that hides the integer pipeline latency;
+//     independent dependency chains per thread, and two 16-warp CTAs per SM,
+//     hide the integer pipeline latency;
+//   * the scale-dependent rounding constants (bits to drop, half-ulp mask)
+//     come from a 256-entry table in shared memory instead of being derived
+//     from the scale on the ALU pipe for every operation;
 //   * C is encoded to posit words once, at the end.
 // The per-element order is exactly the reference-BLAS order, so the result
 // does not depend on BM/BN/BK or the grid.
+//
+// NaR never enters the multiply-add loop: NaR absorbs every operation and
+// no operation on finite posits yields NaR, so C_ij is NaR exactly when beta
+// is NaR, or beta != 0 and C_ij is NaR, or (alpha != 0, k > 0 and) alpha, a
+// word of row i of op(A) or of column j of op(B) is NaR.  Tiles record those
+// rows and columns in shared flags while decoding (NaR words enter the
+// arithmetic as 0) and the epilogue writes NaR where a flag is set.
 #include "internal.cuh"
 
 namespace posit {
 namespace {
 
 constexpr int BM = 128, BN = 64, BK = 16;
-constexpr int TM = 4, TN = 8;
-constexpr int NT = 256;  // (BM / TM) * (BN / TN)
+constexpr int TM = 4, TN = 4;
+constexpr int NT = 512;  // (BM / TM) * (BN / TN)
+constexpr int GM = BM / TM;
 static_assert((BM / TM) * (BN / TN) == NT, "thread tile");
 
 template <int TRI>
@@ -39,22 +50,28 @@ rgemm_kernel(int64_t M, int64_t N, int64_t K, uint32_t alpha,
              uint32_t *__restrict__ C, int64_t ldc, const int32_t *__restrict__ abort_flag) {
   __shared__ __align__(16) pz As[BK][BM];
   __shared__ __align__(16) pz Bs[BK][BN];
+  __shared__ int rowNaR[BM];
+  __shared__ int colNaR[BN];
+  __shared__ pz_rtab rtab[256];
 
   const int tid = threadIdx.x;
-  const int tm = tid & 31;  // row group: rows tm*TM .. +TM-1
-  const int tn = tid >> 5;  // column group (one warp): cols tn*TN .. +TN-1
+  const int tm = tid % GM;  // row group: rows tm*TM .. +TM-1
+  const int tn = tid / GM;  // column group (one warp): cols tn*TN .. +TN-1
   const int64_t m0 = (int64_t)blockIdx.x * BM;
   const int64_t n0 = (int64_t)blockIdx.y * BN;
   if (TRI == TRI_LOWER && n0 > m0 + BM - 1) return;  // tile wholly above diagonal
   if (TRI == TRI_UPPER && m0 > n0 + BN - 1) return;  // tile wholly below diagonal
   if (abort_flag != nullptr && *abort_flag != 0) return;  // a factorisation failed
 
-  const pz alpha_d = pz_decode(alpha);
-  const pz beta_d = pz_decode(beta);
+  const bool all_nar = beta == PZ_NAR_BITS || (alpha == PZ_NAR_BITS && K > 0);
+  for (int i = tid; i < BM; i += NT) rowNaR[i] = 0;
+  for (int j = tid; j < BN; j += NT) colNaR[j] = 0;
+  for (int i = tid; i < 256; i += NT) rtab[i] = pz_rtab_entry(i);
 
   // Accumulators: padding elements (outside C or the triangle) start at 1
   // and are never stored; they only keep the warp on the fast path.
   pz acc[TM][TN];
+  uint32_t c_nar = 0;  // bit i*TN+j: C_ij was NaR (beta != 0)
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
 #pragma unroll
@@ -65,8 +82,14 @@ rgemm_kernel(int64_t M, int64_t N, int64_t K, uint32_t alpha,
         if (beta == 0u) {
           v = pz_zero();
         } else {
-          v = pz_decode(C[r + c * ldc]);
-          if (beta != PZ_ONE_BITS) v = pz_mul(beta_d, v);
+          uint32_t w = C[r + c * ldc];
+          if (w == PZ_NAR_BITS) {
+            c_nar |= 1u << (i * TN + j);
+            v = pz_zero();
+          } else {
+            v = pz_decode(w);
+            if (beta != PZ_ONE_BITS && !all_nar) v = pz_mul_fast(pz_decode(beta), v);
+          }
         }
       }
       acc[i][j] = v;
@@ -83,7 +106,15 @@ rgemm_kernel(int64_t M, int64_t N, int64_t K, uint32_t alpha,
       if (!TA) { r = e % BM; c = e / BM; } else { c = e % BK; r = e / BK; }
       int64_t gr = m0 + r, gk = k0 + c;
       pz v = pz_one();
-      if (gr < M && gk < K) v = pz_decode(TA ? A[gk + gr * lda] : A[gr + gk * lda]);
+      if (gr < M && gk < K) {
+        uint32_t w = TA ? A[gk + gr * lda] : A[gr + gk * lda];
+        if (w == PZ_NAR_BITS) {
+          rowNaR[r] = 1;
+          v = pz_zero();
+        } else {
+          v = pz_decode(w);
+        }
+      }
       As[c][r] = v;
     }
 #pragma unroll
@@ -94,8 +125,15 @@ rgemm_kernel(int64_t M, int64_t N, int64_t K, uint32_t alpha,
       int64_t gk = k0 + r, gc = n0 + c;
       pz v = pz_one();
       if (gk < K && gc < N) {
-        v = pz_decode(TB ? B[gc + gk * ldb] : B[gk + gc * ldb]);
-        if (alpha != PZ_ONE_BITS) v = pz_mul(alpha_d, v);  // t = alpha * op(B)_lj
+        uint32_t w = TB ? B[gc + gk * ldb] : B[gk + gc * ldb];
+        if (w == PZ_NAR_BITS) {
+          colNaR[c] = 1;
+          v = pz_zero();
+        } else {
+          v = pz_decode(w);
+          // t = alpha * op(B)_lj (a NaR alpha is handled by all_nar)
+          if (alpha != PZ_ONE_BITS && !all_nar) v = pz_mul_fast(pz_decode(alpha), v);
+        }
       }
       Bs[r][c] = v;
     }
@@ -112,7 +150,8 @@ rgemm_kernel(int64_t M, int64_t N, int64_t K, uint32_t alpha,
 #pragma unroll
       for (int i = 0; i < TM; ++i) {
 #pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] = pz_add(acc[i][j], pz_mul(b[j], a[i]));
+        for (int j = 0; j < TN; ++j)
+          acc[i][j] = pz_add_tab(rtab, acc[i][j], pz_mul_tab(rtab, b[j], a[i]));
       }
     }
   }
@@ -122,7 +161,12 @@ rgemm_kernel(int64_t M, int64_t N, int64_t K, uint32_t alpha,
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
       int64_t r = m0 + tm * TM + i, c = n0 + tn * TN + j;
-      if (r < M && c < N && tri_ok<TRI>(r, c)) C[r + c * ldc] = pz_to_bits(acc[i][j]);
+      if (r < M && c < N && tri_ok<TRI>(r, c)) {
+        int lr = tm * TM + i, lc = tn * TN + j;
+        bool nar = all_nar || ((c_nar >> (i * TN + j)) & 1u) ||
+                   (kTot > 0 && (rowNaR[lr] | colNaR[lc]));
+        C[r + c * ldc] = nar ? PZ_NAR_BITS : pz_to_bits(acc[i][j]);
+      }
     }
   }
 }

@@ -1,0 +1,145 @@
+"""GPU parity of posit_factor_solve_batched: every problem's factor, pivots,
+info and solution equal the oracle's single-problem results, for several
+launch plans (the plan must not change any bit)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2401_14117_gb300 import binding, inputs
+from paper_2401_14117_gb300.batch import ProblemSet, plan_of
+
+pytestmark = pytest.mark.gpu
+
+L, C = binding.POSIT_LU, binding.POSIT_CHOLESKY
+
+
+def make_set(kinds, ns, nrhs, seed):
+    ps = ProblemSet(kinds, ns, nrhs)
+    host = []
+    for i, (k, n, r) in enumerate(zip(kinds, ns, nrhs)):
+        if k == L:
+            A = oracle.from_double_array(inputs.uniform((n, n), seed + 2 * i))
+        else:
+            A = oracle.from_double_array(inputs.spd(n, seed + 2 * i))
+        B = oracle.from_double_array(inputs.uniform((n, r), seed + 2 * i + 1))
+        ps.set_problem(i, A, B)
+        host.append((A, B))
+    return ps, host
+
+
+def expected(kind, A, B):
+    if kind == L:
+        F, ipiv, info = oracle.rgetrf(A)
+        X = oracle.rgetrs(F, ipiv, B)
+        return F, X, ipiv, info
+    F, info = oracle.rpotrf(A, uplo="L")
+    X = oracle.rpotrs(F, B, uplo="L") if info == 0 else B
+    return F, X, None, info
+
+
+def check(ps, host, idxs=None):
+    for i in (range(ps.count) if idxs is None else idxs):
+        A, B = host[i]
+        F, X, ipiv, info = expected(int(ps.kinds[i]), A, B)
+        gF, gX, gp, ginfo = ps.get_problem(i)
+        n = int(ps.ns[i])
+        assert ginfo == info, (i, ginfo, info)
+        if ps.kinds[i] == L:
+            assert np.array_equal(gF, F), i
+            assert np.array_equal(gp, ipiv), i
+        else:
+            assert np.array_equal(np.tril(gF), np.tril(F)), i
+            assert np.array_equal(np.triu(gF, 1), np.triu(A, 1)), i  # upper untouched
+        assert np.array_equal(gX, X.reshape(n, -1)), i
+
+
+PLANS = [(256, 1, 200 * 1024), (128, 2, 96 * 1024), (512, 1, 48 * 1024), (256, 4, 48 * 1024)]
+
+
+@pytest.mark.parametrize("plan", PLANS)
+def test_batched_matches_oracle(plan):
+    rng = np.random.default_rng(3)
+    count = 40
+    ns = np.concatenate([[1, 2, 3, 200, 300], rng.integers(4, 140, count - 5)])
+    kinds = np.array([L if i % 2 == 0 else C for i in range(count)], np.int32)
+    nrhs = rng.integers(1, 4, count)
+    ps, host = make_set(kinds, ns, nrhs, 100)
+    ps.run(plan_of(*plan))
+    torch.cuda.synchronize()
+    check(ps, host)
+
+
+def test_batched_singular_and_not_positive_definite():
+    kinds = np.array([L, C, L, C], np.int32)
+    ns = np.array([30, 30, 150, 150])
+    nrhs = np.array([2, 2, 1, 1])
+    ps, host = make_set(kinds, ns, nrhs, 7)
+    A0, B0 = host[0]
+    A0 = A0.copy()
+    A0[:, 5] = 0
+    A1, B1 = host[1]
+    A1 = A1.copy()
+    A1[20, 20] = oracle.from_double(-3.0)
+    ps.set_problem(0, A0, B0)
+    ps.set_problem(1, A1, B1)
+    host[0] = (A0, B0)
+    host[1] = (A1, B1)
+    ps.run(plan_of(*PLANS[0]))
+    torch.cuda.synchronize()
+    F, X, ip, info = ps.get_problem(0)
+    assert info == 6
+    F, X, ip, info = ps.get_problem(1)
+    assert info == 21 and np.array_equal(X, B1)
+    check(ps, host, [0, 2, 3])
+
+
+def test_batched_workload_sampled():
+    """4096 problems, n log-uniform in [16, 512], half LU (uniform [-1,1]),
+    half Cholesky (G G^T / n + I), 1 RHS: 160 problems (the largest ones
+    included) compared with the oracle."""
+    count = 4096
+    ns = inputs.batched_sizes(count, inputs.SEED_BASE + 30)
+    kinds = np.array([L if i % 2 == 0 else C for i in range(count)], np.int32)
+    nrhs = np.ones(count, np.int64)
+    ps = ProblemSet(kinds, ns, nrhs)
+    rng = np.random.default_rng(5)
+    big = np.argsort(-ns)[:6]
+    sample = sorted(set(big.tolist()) | set(rng.integers(0, count, 154).tolist()))
+    host = {}
+    for i in range(count):
+        n = int(ns[i])
+        if kinds[i] == L:
+            A = oracle.from_double_array(inputs.uniform((n, n), 50000 + i))
+        else:
+            A = oracle.from_double_array(inputs.spd(n, 50000 + i))
+        B = oracle.from_double_array(inputs.uniform((n, 1), 90000 + i))
+        ps.set_problem(i, A, B)
+        if i in sample:
+            host[i] = (A, B)
+    ps.run(plan_of(256, 1, 200 * 1024))
+    torch.cuda.synchronize()
+    for i in sample:
+        A, B = host[i]
+        F, X, ipiv, info = expected(int(kinds[i]), A, B)
+        gF, gX, gp, ginfo = ps.get_problem(i)
+        assert ginfo == info == 0
+        if kinds[i] == L:
+            assert np.array_equal(gF, F) and np.array_equal(gp, ipiv), i
+        else:
+            assert np.array_equal(np.tril(gF), np.tril(F)), i
+        assert np.array_equal(gX, X), i
+
+
+def test_batched_argument_errors():
+    plan = plan_of(256, 1, 48 * 1024)
+    with pytest.raises(binding.PositError) as e:
+        binding.posit_factor_solve_batched(-1, None, None, 1, 1, plan, None)
+    assert e.value.code == -1
+    with pytest.raises(binding.PositError) as e:
+        binding.posit_factor_solve_batched(1, None, None, 1, 1, plan, None)
+    assert e.value.code == -2
+    with pytest.raises(binding.PositError) as e:
+        binding.posit_factor_solve_batched(0, None, None, 1, 1, plan_of(100, 1, 0), None)
+    assert e.value.code == -6
+    binding.posit_factor_solve_batched(0, None, None, 0, 0, plan, None)

@@ -28,7 +28,8 @@ def run_gpu(ta, tb, alpha, A, B, beta, C):
     m, n = C.shape
     k = A.shape[0] if ta == "T" else A.shape[1]
     dA, dB, dC = to_dev(A), to_dev(B), to_dev(C)
-    binding.posit_rgemm(ta, tb, m, n, k, alpha, dA, A.shape[0], dB, B.shape[0], beta, dC, m)
+    binding.posit_rgemm(ta, tb, m, n, k, alpha, dA, max(1, A.shape[0]), dB, max(1, B.shape[0]),
+                        beta, dC, max(1, m))
     torch.cuda.synchronize()
     return from_dev(dC)
 
@@ -68,7 +69,8 @@ def test_special_values_inside_matrices():
     A[3, :] = 0x80000000
     B[:, 5] = 0
     C = mixed_words(rng, m * n).reshape(m, n)
-    for alpha, beta in ((ONE, ONE), (0x7FFFFFFF, 0x00000001), (0x48000000, 0)):
+    for alpha, beta in ((ONE, ONE), (0x7FFFFFFF, 0x00000001), (0x48000000, 0),
+                        (0x80000000, ONE), (ONE, 0x80000000), (0, 0x80000000)):
         assert_same(run_gpu("N", "N", alpha, A, B, beta, C), oracle.rgemm("N", "N", alpha, A, B, beta, C))
 
 
