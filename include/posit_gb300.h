@@ -216,9 +216,13 @@ typedef struct posit_plan {
   int32_t reserved;
 } posit_plan;
 
+/* Bytes of DEVICE workspace posit_factor_solve_batched needs for problems up
+   to max_n x max_n with up to max_nrhs right-hand sides under `plan`
+   (written to *bytes).  Errors: -1 max_n, -2 max_nrhs, -3 plan, -4 bytes. */
 POSIT_API int posit_batched_workspace_size(int64_t max_n, int64_t max_nrhs,
                                            const posit_plan *plan, size_t *bytes);
 
+/* The batched call described above. */
 POSIT_API int posit_factor_solve_batched(int64_t count, const posit_problem *problems,
                                          const int32_t *order, int64_t max_n, int64_t max_nrhs,
                                          const posit_plan *plan, void *workspace,
