@@ -37,10 +37,11 @@ METRIC = "Posit(32,2) Rgemm/Rgetrf Gflops vs INT-issue roofline; served-solve p5
 UNIT = "Gflops"
 ONE = 0x40000000
 
-# Warp instructions the rgemm kernel issues per posit multiply-add, from
-# smsp__inst_executed.sum of one ncu launch (see profiles/); None until
-# measured for the current kernel.
-INST_PER_MAC = None
+# Warp instructions the rgemm kernel issues per posit multiply-add:
+# smsp__inst_executed.sum / (M N K) of one ncu capture of the current kernel
+# (NN, 2048^3, uniform [-1,1]: 2.3357e10 / 8.590e9; profiles/rgemm_nn_ncu.md).
+# The count is set by the inner loop, so it scales with M N K.
+INST_PER_MAC = 2.7191
 SM_COUNT = 152
 SCHEDULERS_PER_SM = 4
 

@@ -228,6 +228,85 @@ POSIT_API int posit_factor_solve_batched(int64_t count, const posit_problem *pro
                                          const posit_plan *plan, void *workspace,
                                          cudaStream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * Serving: a continuous-batching server for factor+solve requests (the
+ * request-serving pattern over the paper's Rgetrf+Rgetrs / Rpotrf+Rpotrs).
+ *
+ * Requests carry HOST matrices (column-major, ld = n); the caller keeps A
+ * and B readable until the request is admitted and X / info writable until
+ * it completes (page-locked host memory lets the copies overlap).  Requests
+ * are admitted in arrival order while their device state (A, B, pivots,
+ * info) fits budget_bytes; it stays on the device until completion.  Requests
+ * with n <= small_n_max are batched continuously: when the previous small
+ * launch has finished, every admitted, not yet started small request (up to
+ * max_batch) goes into one persistent posit_factor_solve_batched launch with
+ * `plan`.  Larger requests run one at a time through the blocked multi-SM
+ * routines on a second stream, concurrently with the small lane.  X receives
+ * the solution (LU: posit_rgetrs 'N'; Cholesky: posit_rpotrs 'L', or B
+ * unchanged if the factorisation failed) and *info the factorisation's info,
+ * bit-identical to the single-request routines whatever the mix.
+ *
+ * The server is driven by its caller: posit_serve_poll retires finished
+ * launches (non-blocking event queries), frees their memory, admits waiting
+ * requests, starts launches on idle lanes, and returns the tags of the
+ * requests completed since the previous poll.  Not thread-safe: one thread
+ * drives one server.
+ * ------------------------------------------------------------------------ */
+typedef struct posit_serve_config {
+  int64_t budget_bytes;  /* device memory for resident request state */
+  int32_t small_n_max;   /* n <= this: batched lane */
+  int32_t max_batch;     /* requests per batched launch */
+  int32_t max_nrhs;      /* largest nrhs accepted */
+  int32_t reserved;
+  posit_plan plan;       /* batched launch shape */
+} posit_serve_config;
+
+typedef struct posit_request {
+  int32_t kind;          /* POSIT_LU or POSIT_CHOLESKY */
+  int32_t n;
+  int32_t nrhs;
+  int32_t reserved;
+  const posit32_t *A;    /* HOST, n x n */
+  const posit32_t *B;    /* HOST, n x nrhs */
+  posit32_t *X;          /* HOST, n x nrhs, written at completion */
+  int32_t *info;         /* HOST, written at completion */
+  uint64_t tag;          /* returned by posit_serve_poll */
+} posit_request;
+
+typedef struct posit_serve_stats_t {
+  int64_t pending;             /* submitted, waiting for memory */
+  int64_t admitted;            /* total admitted */
+  int64_t completed;           /* total completed */
+  int64_t inflight_launches;
+  int64_t launches;            /* total launches started */
+  int64_t device_bytes_in_use;
+  int64_t batched_requests;    /* requests that went through the small lane */
+  int64_t largest_batch;       /* most requests in one small-lane launch */
+} posit_serve_stats_t;
+
+typedef struct posit_server posit_server;
+
+/* Create a server (streams, batched workspace, staging).  Errors: -1 cfg,
+   -2 out NULL, POSIT_ERR_ALLOC / POSIT_ERR_CUDA. */
+POSIT_API int posit_serve_open(const posit_serve_config *cfg, posit_server **out);
+
+/* Queue a request (copied; host pointers are used later, see above).
+   Errors: -1 server NULL, -2 bad request (kind, sizes, NULL pointers, or a
+   footprint larger than the whole budget). */
+POSIT_API int posit_serve_submit(posit_server *server, const posit_request *req);
+
+/* Make progress and collect up to max_done completed tags into done_tags
+   (*n_done receives the count).  Never blocks on the GPU.
+   Errors: -1 server NULL, -3 done_tags/max_done, -4 n_done NULL. */
+POSIT_API int posit_serve_poll(posit_server *server, uint64_t *done_tags, int64_t max_done,
+                               int64_t *n_done);
+
+/* Counters of the server (host memory).  Errors: -1 server, -2 st NULL. */
+POSIT_API int posit_serve_stats(const posit_server *server, posit_serve_stats_t *st);
+
+/* Wait for the server's streams, free everything.  Errors: -1 server NULL. */
+POSIT_API int posit_serve_close(posit_server *server);
+
 #ifdef __cplusplus
 }
 #endif

@@ -38,6 +38,11 @@ _SIGS = {
     "posit_rpotrs": [c_char, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp],
     "posit_batched_workspace_size": [c_i64, c_i64, c_vp, c_vp],
     "posit_factor_solve_batched": [c_i64, c_vp, c_vp, c_i64, c_i64, c_vp, c_vp, c_vp],
+    "posit_serve_open": [c_vp, c_vp],
+    "posit_serve_submit": [c_vp, c_vp],
+    "posit_serve_poll": [c_vp, c_vp, c_i64, c_vp],
+    "posit_serve_stats": [c_vp, c_vp],
+    "posit_serve_close": [c_vp],
 }
 
 POSIT_LU = 0
@@ -47,6 +52,25 @@ POSIT_CHOLESKY = 1
 class posit_plan(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("smem_bytes", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class posit_serve_config(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_int64), ("small_n_max", ctypes.c_int32),
+                ("max_batch", ctypes.c_int32), ("max_nrhs", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("plan", posit_plan)]
+
+
+class posit_request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n", ctypes.c_int32), ("nrhs", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("A", ctypes.c_void_p), ("B", ctypes.c_void_p),
+                ("X", ctypes.c_void_p), ("info", ctypes.c_void_p), ("tag", ctypes.c_uint64)]
+
+
+class posit_serve_stats_t(ctypes.Structure):
+    _fields_ = [("pending", ctypes.c_int64), ("admitted", ctypes.c_int64),
+                ("completed", ctypes.c_int64), ("inflight_launches", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("device_bytes_in_use", ctypes.c_int64),
+                ("batched_requests", ctypes.c_int64), ("largest_batch", ctypes.c_int64)]
 
 
 # layout of struct posit_problem (include/posit_gb300.h), for building the
@@ -171,3 +195,31 @@ def posit_factor_solve_batched(count, problems, order, max_n, max_nrhs, plan, wo
     return _check("posit_factor_solve_batched", lib().posit_factor_solve_batched(
         count, _ptr(problems), _ptr(order), max_n, max_nrhs, ctypes.byref(plan),
         _ptr(workspace), _stream(stream)))
+
+
+def posit_serve_open(cfg):
+    h = ctypes.c_void_p()
+    _check("posit_serve_open", lib().posit_serve_open(ctypes.byref(cfg), ctypes.byref(h)))
+    return h.value
+
+
+def posit_serve_submit(server, req):
+    return _check("posit_serve_submit", lib().posit_serve_submit(server, ctypes.byref(req)))
+
+
+def posit_serve_poll(server, tags_buf, max_done):
+    """tags_buf: ctypes array of c_uint64; returns the number of tags written."""
+    n = ctypes.c_int64(0)
+    _check("posit_serve_poll", lib().posit_serve_poll(server, tags_buf, max_done, ctypes.byref(n)))
+    return n.value
+
+
+def posit_serve_stats(server):
+    st = posit_serve_stats_t()
+    _check("posit_serve_stats", lib().posit_serve_stats(server, ctypes.byref(st)))
+    return st
+
+
+def posit_serve_close(server):
+    return _check("posit_serve_close", lib().posit_serve_close(server))
+

@@ -53,6 +53,10 @@ int getrs_run(bool trans, int64_t n, int64_t nrhs, const uint32_t *A, int64_t ld
               const int32_t *ipiv, uint32_t *B, int64_t ldb, void *scratch, cudaStream_t stream);
 int potrs_run(bool upper, int64_t n, int64_t nrhs, const uint32_t *A, int64_t lda, uint32_t *B,
               int64_t ldb, void *scratch, cudaStream_t stream);
+// Same, skipped on the device when *abort_flag != 0 (a failed factorisation).
+int potrs_run_guarded(bool upper, int64_t n, int64_t nrhs, const uint32_t *A, int64_t lda,
+                      uint32_t *B, int64_t ldb, const int32_t *abort_flag, void *scratch,
+                      cudaStream_t stream);
 
 // Batched factor + solve (batched.cu).
 size_t batched_workspace_bytes(int max_n, int max_nrhs, const posit_plan &plan);

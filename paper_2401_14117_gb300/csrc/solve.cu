@@ -77,6 +77,7 @@ struct TriArgs {
   int bpc;       // blocks per CTA
   unsigned *bar;
   int *err;
+  const int32_t *abort_flag;  // skip the solve when *abort_flag != 0
 };
 
 __device__ __forceinline__ uint32_t tri_at(const TriArgs &a, int64_t i, int64_t k) {
@@ -99,6 +100,7 @@ __global__ void __launch_bounds__(ST, 1) trsv_wave_kernel(TriArgs a) {
   const int g = blockIdx.x;
   const unsigned G = gridDim.x;
   const int J0 = g * a.bpc, J1 = min(a.nblk, (g + 1) * a.bpc);
+  if (a.abort_flag && *(volatile const int32_t *)a.abort_flag != 0) return;  // all CTAs alike
 
   // load own rows of B
   for (int J = J0; J < J1; ++J) {
@@ -180,13 +182,15 @@ __global__ void __launch_bounds__(ST, 1) trsv_wave_kernel(TriArgs a) {
 // A[k + i*lda] (column i below the diagonal).
 __global__ void __launch_bounds__(ST) trsv_dot_backward_kernel(const uint32_t *__restrict__ A,
                                                                 int64_t lda, uint32_t *B,
-                                                                int64_t ldb, int64_t n, int unit) {
+                                                                int64_t ldb, int64_t n, int unit,
+                                                                const int32_t *abort_flag) {
   __shared__ pz prod[ST];
   __shared__ pz acc_s;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pz *x = reinterpret_cast<pz *>(smem_raw);  // [n] the right-hand side / solution
   uint32_t *b = B + (int64_t)blockIdx.x * ldb;
   const int tid = threadIdx.x;
+  if (abort_flag && *abort_flag != 0) return;
   for (int64_t i = tid; i < n; i += ST) x[i] = pz_decode(b[i]);
   __syncthreads();
   for (int64_t i = n - 1; i >= 0; --i) {
@@ -251,9 +255,11 @@ __global__ void laswp_vec_global_kernel(uint32_t *B, int64_t ldb, int64_t n,
 }
 
 __global__ void trsv_dot_backward_global_kernel(const uint32_t *__restrict__ A, int64_t lda,
-                                                uint32_t *B, int64_t ldb, int64_t n, int unit) {
+                                                uint32_t *B, int64_t ldb, int64_t n, int unit,
+                                                const int32_t *abort_flag) {
   // columns too long for shared memory: one thread per right-hand side
   if (threadIdx.x != 0) return;
+  if (abort_flag && *abort_flag != 0) return;
   uint32_t *b = B + (int64_t)blockIdx.x * ldb;
   for (int64_t i = n - 1; i >= 0; --i) {
     const uint32_t *col = A + i * lda;
@@ -298,7 +304,7 @@ constexpr size_t kWaveScratch = 256;
 
 int trsv_wave(const uint32_t *A, int64_t lda, int trans, int backward, int unit, uint32_t *B,
               int64_t ldb, int64_t n, int64_t nrhs, void *scratch, const Limits &l,
-              cudaStream_t stream) {
+              cudaStream_t stream, const int32_t *abort_flag = nullptr) {
   const int nblk = (int)ceil_div(n, WBS);
   for (int64_t c0 = 0; c0 < nrhs; c0 += NRHS_CHUNK) {
     const int nr = (int)min64(NRHS_CHUNK, nrhs - c0);
@@ -316,6 +322,7 @@ int trsv_wave(const uint32_t *A, int64_t lda, int trans, int backward, int unit,
     ta.trans = trans; ta.backward = backward; ta.unit = unit; ta.nblk = nblk; ta.bpc = bpc;
     ta.bar = static_cast<unsigned *>(scratch);
     ta.err = reinterpret_cast<int *>(static_cast<char *>(scratch) + 2 * sizeof(unsigned));
+    ta.abort_flag = abort_flag;
     void *args[] = {&ta};
     if (cudaLaunchCooperativeKernel((const void *)trsv_wave_kernel, dim3(G), dim3(ST), args, smem,
                                     stream) != cudaSuccess)
@@ -325,15 +332,18 @@ int trsv_wave(const uint32_t *A, int64_t lda, int trans, int backward, int unit,
 }
 
 int trsv_dot_backward(const uint32_t *A, int64_t lda, int unit, uint32_t *B, int64_t ldb,
-                      int64_t n, int64_t nrhs, const Limits &l, cudaStream_t stream) {
+                      int64_t n, int64_t nrhs, const Limits &l, cudaStream_t stream,
+                      const int32_t *abort_flag = nullptr) {
   size_t smem = (size_t)n * sizeof(pz);
   if (smem + 4096 <= (size_t)l.smem_optin) {
     if (cudaFuncSetAttribute(trsv_dot_backward_kernel,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return POSIT_ERR_CUDA;
-    trsv_dot_backward_kernel<<<(unsigned)nrhs, ST, smem, stream>>>(A, lda, B, ldb, n, unit);
+    trsv_dot_backward_kernel<<<(unsigned)nrhs, ST, smem, stream>>>(A, lda, B, ldb, n, unit,
+                                                                   abort_flag);
   } else {
-    trsv_dot_backward_global_kernel<<<(unsigned)nrhs, 32, 0, stream>>>(A, lda, B, ldb, n, unit);
+    trsv_dot_backward_global_kernel<<<(unsigned)nrhs, 32, 0, stream>>>(A, lda, B, ldb, n, unit,
+                                                                       abort_flag);
   }
   return launch_status();
 }
@@ -361,21 +371,29 @@ int getrs_run(bool trans, int64_t n, int64_t nrhs, const uint32_t *A, int64_t ld
   return laswp_vec(B, ldb, n, nrhs, ipiv, true, l, stream);
 }
 
-int potrs_run(bool upper, int64_t n, int64_t nrhs, const uint32_t *A, int64_t lda, uint32_t *B,
-              int64_t ldb, void *scratch, cudaStream_t stream) {
+int potrs_run_guarded(bool upper, int64_t n, int64_t nrhs, const uint32_t *A, int64_t lda,
+                      uint32_t *B, int64_t ldb, const int32_t *abort_flag, void *scratch,
+                      cudaStream_t stream) {
   Limits l;
   int st = limits(l);
   if (st) return st;
   if (!upper) {
     // L y = b: ascending, then divide
-    if ((st = trsv_wave(A, lda, 0, 0, 0, B, ldb, n, nrhs, scratch, l, stream))) return st;
+    if ((st = trsv_wave(A, lda, 0, 0, 0, B, ldb, n, nrhs, scratch, l, stream, abort_flag)))
+      return st;
     // L^T x = y: dot form, k ascending -- serial chain
-    return trsv_dot_backward(A, lda, 0, B, ldb, n, nrhs, l, stream);
+    return trsv_dot_backward(A, lda, 0, B, ldb, n, nrhs, l, stream, abort_flag);
   }
   // U^T y = b: ascending dot form
-  if ((st = trsv_wave(A, lda, 1, 0, 0, B, ldb, n, nrhs, scratch, l, stream))) return st;
+  if ((st = trsv_wave(A, lda, 1, 0, 0, B, ldb, n, nrhs, scratch, l, stream, abort_flag)))
+    return st;
   // U x = y: descending, column order
-  return trsv_wave(A, lda, 0, 1, 0, B, ldb, n, nrhs, scratch, l, stream);
+  return trsv_wave(A, lda, 0, 1, 0, B, ldb, n, nrhs, scratch, l, stream, abort_flag);
+}
+
+int potrs_run(bool upper, int64_t n, int64_t nrhs, const uint32_t *A, int64_t lda, uint32_t *B,
+              int64_t ldb, void *scratch, cudaStream_t stream) {
+  return potrs_run_guarded(upper, n, nrhs, A, lda, B, ldb, nullptr, scratch, stream);
 }
 
 }  // namespace posit

@@ -1,0 +1,90 @@
+"""The continuous-batching server: every served result equals the result of
+the same problem solved alone (single-problem routines) -- and, for the
+smaller problems, the CPU oracle -- whatever else was in flight."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2401_14117_gb300 import binding, serving
+
+pytestmark = pytest.mark.gpu
+
+
+def alone(pool, i):
+    """The single-problem routines on one pool problem (device)."""
+    n, r = int(pool.ns[i]), int(pool.nrhs[i])
+    A = pool.A[i].cuda().clone()
+    B = pool.B[i].cuda().clone()
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    if pool.kinds[i] == binding.POSIT_LU:
+        ipiv = torch.zeros(n, dtype=torch.int32, device="cuda")
+        binding.posit_rgetrf(n, n, A, n, ipiv, info)
+        binding.posit_rgetrs("N", n, r, A, n, ipiv, B, n)
+    else:
+        binding.posit_rpotrf("L", n, A, n, info)
+        torch.cuda.synchronize()
+        if int(info.item()) == 0:
+            binding.posit_rpotrs("L", n, r, A, n, B, n)
+    torch.cuda.synchronize()
+    return B.cpu().numpy().view(np.uint32).reshape(-1), int(info.item())
+
+
+def oracle_solution(pool, i):
+    n, r = int(pool.ns[i]), int(pool.nrhs[i])
+    A = pool.A[i].numpy().view(np.uint32).reshape(n, n).T
+    B = pool.B[i].numpy().view(np.uint32).reshape(r, n).T
+    if pool.kinds[i] == binding.POSIT_LU:
+        F, ipiv, info = oracle.rgetrf(A)
+        X = oracle.rgetrs(F, ipiv, B)
+    else:
+        F, info = oracle.rpotrf(A)
+        X = oracle.rpotrs(F, B) if info == 0 else B
+    return np.asfortranarray(X).ravel(order="F"), info
+
+
+@pytest.mark.parametrize("small_n_max", [96, 512])
+def test_served_results_equal_alone_and_oracle(small_n_max):
+    pool = serving.Pool(20, 16, 700, 4, seed=77)
+    t, idx = serving.arrivals(400.0, 1.5, pool.size, seed=78)
+    cfg = serving.default_config(budget_gb=2.0, small_n_max=small_n_max, max_batch=64)
+    res = serving.run(pool, t, idx, cfg, duration=1.5, max_outstanding=64,
+                      capture=set(range(len(t))), drain=True)
+    assert res["completed"] == res["submitted"] == res["offered"] > 20
+    assert res["launches"] >= 2
+    alone_x = {}
+    for rid, (x, info) in res["kept"].items():
+        i = int(idx[rid])
+        if i not in alone_x:
+            alone_x[i] = alone(pool, i)
+        ax, ainfo = alone_x[i]
+        assert info == ainfo and np.array_equal(x, ax), (rid, i)
+    # the smaller problems also against the oracle
+    for i in sorted(alone_x):
+        if pool.ns[i] <= 200:
+            ox, oinfo = oracle_solution(pool, i)
+            assert alone_x[i][1] == oinfo and np.array_equal(alone_x[i][0], ox), i
+
+
+def test_continuous_batching_forms_batches():
+    pool = serving.Pool(16, 16, 128, 2, seed=5)
+    t, idx = serving.arrivals(4000.0, 0.5, pool.size, seed=6)
+    cfg = serving.default_config(budget_gb=1.0, small_n_max=512, max_batch=256)
+    res = serving.run(pool, t, idx, cfg, duration=0.5, max_outstanding=256, drain=True)
+    assert res["completed"] == res["offered"]
+    assert res["largest_batch"] > 1
+    assert res["batched_requests"] == res["completed"]
+
+
+def test_budget_too_small_for_a_request_is_rejected():
+    cfg = serving.default_config(budget_gb=1e-6)
+    server = binding.posit_serve_open(cfg)
+    try:
+        A = torch.zeros(64 * 64, dtype=torch.int32, pin_memory=True)
+        req = binding.posit_request(binding.POSIT_LU, 64, 1, 0, A.data_ptr(), A.data_ptr(),
+                                    A.data_ptr(), A.data_ptr(), 0)
+        with pytest.raises(binding.PositError) as e:
+            binding.posit_serve_submit(server, req)
+        assert e.value.code == -2
+    finally:
+        binding.posit_serve_close(server)
