@@ -53,6 +53,7 @@ typedef uint32_t posit32_t;
 #define POSIT_ERR_ALLOC (-1002)   /* stream-ordered scratch allocation failed */
 #define POSIT_ERR_TIMEOUT (-1003) /* a bounded device-side wait gave up */
 #define POSIT_ERR_DEVICE (-1004)  /* no usable device */
+#define POSIT_ERR_SCRATCH (-1005) /* posit_rgetrf_static: the fixed scratch is too small */
 
 /* ---------------------------------------------------------------------------
  * Conversion and element-wise arithmetic (the paper's Add/Mul/Div/Sqrt
@@ -306,6 +307,28 @@ POSIT_API int posit_serve_stats(const posit_server *server, posit_serve_stats_t 
 
 /* Wait for the server's streams, free everything.  Errors: -1 server NULL. */
 POSIT_API int posit_serve_close(posit_server *server);
+
+/* ---------------------------------------------------------------------------
+ * posit_rgetrf_static: posit_rgetrf for callers that must not allocate.
+ * (The paper has no counterpart; this is a library convenience.)
+ *
+ * Same arguments, results (bit for bit) and errors as posit_rgetrf, but the
+ * routine makes no device allocation: its ~0.6 MB of scratch comes from a
+ * fixed 1 MiB array compiled into the library, which every GPU that loads
+ * the library keeps for the life of the process.  Meant for callers whose
+ * device memory is fully held by another allocator, that run under strict
+ * memory accounting, or that must not wait on an allocation.
+ * - The first call on a device looks up the array's device address (once
+ *   per device, with that device current); make that first call before any
+ *   stream capture begins.
+ * - All calls share the one array: calls whose work overlaps on the GPU
+ *   (for example on two streams at once) race and give wrong results, so
+ *   order them on one stream or synchronise between them.
+ * - Returns POSIT_ERR_SCRATCH if the device would need more scratch than
+ *   the array holds (devices with more than about 250 SMs).
+ * ------------------------------------------------------------------------ */
+POSIT_API int posit_rgetrf_static(int64_t m, int64_t n, posit32_t *A, int64_t lda,
+                                  int32_t *ipiv, int32_t *info, cudaStream_t stream);
 
 #ifdef __cplusplus
 }

@@ -43,6 +43,7 @@ _SIGS = {
     "posit_serve_poll": [c_vp, c_vp, c_i64, c_vp],
     "posit_serve_stats": [c_vp, c_vp],
     "posit_serve_close": [c_vp],
+    "posit_rgetrf_static": [c_i64, c_i64, c_vp, c_i64, c_vp, c_vp, c_vp],
 }
 
 POSIT_LU = 0
@@ -223,3 +224,8 @@ def posit_serve_stats(server):
 def posit_serve_close(server):
     return _check("posit_serve_close", lib().posit_serve_close(server))
 
+
+def posit_rgetrf_static(m, n, A, lda, ipiv, info, stream=None):
+    """posit_rgetrf without any device allocation (fixed scratch in the library)."""
+    return _check("posit_rgetrf_static", lib().posit_rgetrf_static(
+        m, n, _ptr(A), lda, _ptr(ipiv), _ptr(info), _stream(stream)))
