@@ -177,7 +177,10 @@ POSIT_API int posit_rpotrs(char uplo, int64_t n, int64_t nrhs, const posit32_t *
  *                        solution of A X = B as posit_rgetrs('N') gives it;
  *   kind POSIT_CHOLESKY: the lower triangle of A is overwritten by L as
  *                        posit_rpotrf('L') does and B by the posit_rpotrs('L')
- *                        solution (B is left unchanged if info > 0).
+ *                        solution (B is left unchanged if info > 0);
+ *   kind POSIT_CHOLESKY_U: the same with the upper triangle, A = U^T U,
+ *                        posit_rpotrf('U') and posit_rpotrs('U'), whose
+ *                        solve has no serial chain.
  * *info (device int32, may be NULL) receives the factorisation's info.
  * Every output word equals the corresponding single-problem routine's.
  * order: optional DEVICE array (count int32): the problems are started in
@@ -195,10 +198,11 @@ POSIT_API int posit_rpotrs(char uplo, int64_t n, int64_t nrhs, const posit32_t *
  * Errors: -1 count, -2 problems NULL, -4 max_n, -5 max_nrhs, -6 plan.
  * ------------------------------------------------------------------------ */
 #define POSIT_LU 0
-#define POSIT_CHOLESKY 1
+#define POSIT_CHOLESKY 1    /* uplo 'L' */
+#define POSIT_CHOLESKY_U 2  /* uplo 'U' */
 
 typedef struct posit_problem {
-  int32_t kind;      /* POSIT_LU or POSIT_CHOLESKY */
+  int32_t kind;      /* POSIT_LU, POSIT_CHOLESKY or POSIT_CHOLESKY_U */
   int32_t n;
   int32_t nrhs;
   int32_t reserved;
@@ -241,10 +245,12 @@ POSIT_API int posit_factor_solve_batched(int64_t count, const posit_problem *pro
  * with n <= small_n_max are batched continuously: when the previous small
  * launch has finished, every admitted, not yet started small request (up to
  * max_batch) goes into one persistent posit_factor_solve_batched launch with
- * `plan`.  Larger requests run one at a time through the blocked multi-SM
- * routines on a second stream, concurrently with the small lane.  X receives
- * the solution (LU: posit_rgetrs 'N'; Cholesky: posit_rpotrs 'L', or B
- * unchanged if the factorisation failed) and *info the factorisation's info,
+ * `plan`.  Larger requests run through the blocked multi-SM routines, up to
+ * large_lanes of them at once on their own streams, concurrently with the
+ * small lane.  X receives
+ * the solution (LU: posit_rgetrs 'N'; Cholesky: posit_rpotrs 'L' or, for
+ * POSIT_CHOLESKY_U, 'U' -- or B unchanged if the factorisation failed) and
+ * *info the factorisation's info,
  * bit-identical to the single-request routines whatever the mix.
  *
  * The server is driven by its caller: posit_serve_poll retires finished
@@ -258,12 +264,12 @@ typedef struct posit_serve_config {
   int32_t small_n_max;   /* n <= this: batched lane */
   int32_t max_batch;     /* requests per batched launch */
   int32_t max_nrhs;      /* largest nrhs accepted */
-  int32_t reserved;
+  int32_t large_lanes;   /* concurrent large requests (streams); 0 means 16 */
   posit_plan plan;       /* batched launch shape */
 } posit_serve_config;
 
 typedef struct posit_request {
-  int32_t kind;          /* POSIT_LU or POSIT_CHOLESKY */
+  int32_t kind;          /* POSIT_LU, POSIT_CHOLESKY or POSIT_CHOLESKY_U */
   int32_t n;
   int32_t nrhs;
   int32_t reserved;

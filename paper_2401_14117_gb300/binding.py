@@ -47,7 +47,8 @@ _SIGS = {
 }
 
 POSIT_LU = 0
-POSIT_CHOLESKY = 1
+POSIT_CHOLESKY = 1     # uplo 'L'
+POSIT_CHOLESKY_U = 2   # uplo 'U'
 
 
 class posit_plan(ctypes.Structure):
@@ -58,7 +59,7 @@ class posit_plan(ctypes.Structure):
 class posit_serve_config(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_int64), ("small_n_max", ctypes.c_int32),
                 ("max_batch", ctypes.c_int32), ("max_nrhs", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("plan", posit_plan)]
+                ("large_lanes", ctypes.c_int32), ("plan", posit_plan)]
 
 
 class posit_request(ctypes.Structure):

@@ -123,6 +123,62 @@ __device__ int chol_decoded(pz *M, int n, pz *sh) {
   return 0;
 }
 
+// Cholesky (upper, A = U^T U) of the decoded matrix; returns info.  The
+// transposed mirror of chol_decoded: row j is scaled, the trailing upper
+// triangle updated.
+__device__ int chol_decoded_upper(pz *M, int n, pz *sh) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int j = 0; j < n; ++j) {
+    pz d = M[j + (size_t)j * n];
+    if (pz_is_nar(d) || pz_is_zero(d) || (d.m >> 31)) return j + 1;
+    if (tid == 0) {
+      pz s = pz_sqrt(d);
+      sh[0] = s;
+      sh[1] = pz_div(pz_one(), s);
+    }
+    __syncthreads();
+    if (tid == 0) M[j + (size_t)j * n] = sh[0];
+    const pz r = sh[1];
+    for (int k = j + 1 + tid; k < n; k += nt) M[j + (size_t)k * n] = pz_mul(M[j + (size_t)k * n], r);
+    __syncthreads();
+    const int m = n - j - 1;
+    for (int idx = tid; idx < m * m; idx += nt) {
+      int i = j + 1 + idx % m, k = j + 1 + idx / m;
+      if (i > k) continue;
+      pz *x = &M[i + (size_t)k * n];
+      *x = pz_sub(*x, pz_mul(M[j + (size_t)i * n], M[j + (size_t)k * n]));
+    }
+    __syncthreads();
+  }
+  return 0;
+}
+
+// Rpotrs 'U' on the decoded factor: U^T y = b (updates from k ascending,
+// then / u_ii), U x = y (updates from k descending, then / u_ii); both run
+// column by column with the rows in parallel.
+__device__ void potrs_decoded_upper(const pz *M, int n, pz *X, int nrhs) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int k = 0; k < n; ++k) {
+    for (int c = tid; c < nrhs; c += nt) X[k + c * n] = pz_div(X[k + c * n], M[k + (size_t)k * n]);
+    __syncthreads();
+    const int m = n - k - 1;
+    for (int idx = tid; idx < m * nrhs; idx += nt) {
+      int i = k + 1 + idx % m, c = idx / m;
+      X[i + c * n] = pz_sub(X[i + c * n], pz_mul(M[k + (size_t)i * n], X[k + c * n]));
+    }
+    __syncthreads();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    for (int c = tid; c < nrhs; c += nt) X[k + c * n] = pz_div(X[k + c * n], M[k + (size_t)k * n]);
+    __syncthreads();
+    for (int idx = tid; idx < k * nrhs; idx += nt) {
+      int i = idx % k, c = idx / k;
+      X[i + c * n] = pz_sub(X[i + c * n], pz_mul(M[i + (size_t)k * n], X[k + c * n]));
+    }
+    __syncthreads();
+  }
+}
+
 // Rgetrs 'N' on decoded factors: swaps, L y = b (unit), U x = y.
 __device__ void getrs_decoded(const pz *M, int n, const int32_t *ipiv, pz *X, int nrhs) {
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -166,18 +222,26 @@ __device__ void potrs_decoded(const pz *M, int n, pz *X, int nrhs, pz *prod) {
     }
     __syncthreads();
   }
-  // x_i = (y_i - sum_{k>i, ascending} l_ki x_k) / l_ii: products in parallel,
-  // one serial chain of subtractions per right-hand side
+  // x_i = (y_i - sum_{k>i, ascending} l_ki x_k) / l_ii: products in parallel
+  // (stored negated), one serial chain of fast additions per right-hand side;
+  // a NaR product or y_i makes x_i NaR
   for (int i = n - 1; i >= 0; --i) {
     const int m = n - i - 1;
     for (int idx = tid; idx < m * nrhs; idx += nt) {
       int k = i + 1 + idx % m, c = idx / m;
-      prod[idx] = pz_mul(M[k + (size_t)i * n], X[k + c * n]);
+      pz p = pz_mul(M[k + (size_t)i * n], X[k + c * n]);
+      prod[idx] = pz{p.s, p.m ^ 0x80000000u};
     }
     __syncthreads();
     for (int c = tid; c < nrhs; c += nt) {
       pz acc = X[i + c * n];
-      for (int t = 0; t < m; ++t) acc = pz_sub(acc, prod[t + c * m]);
+      bool nar = pz_is_nar(acc);
+      for (int t = 0; t < m; ++t) {
+        pz p = prod[t + c * m];
+        nar |= p.s >= PZ_NAR_T;
+        acc = pz_add_fast(acc, p);
+      }
+      acc = nar ? pz_nar() : pz_canon(acc, false);
       X[i + c * n] = pz_div(acc, M[i + (size_t)i * n]);
     }
     __syncthreads();
@@ -210,9 +274,11 @@ __global__ void batched_kernel(const posit_problem *__restrict__ probs,
     pz *M = need <= (size_t)smem_elems ? sm : ws;
     pz *X = M + (size_t)n * n;
     pz *prod = X + (size_t)n * nrhs;
+    const bool lower_only = P.kind == POSIT_CHOLESKY, upper_only = P.kind == POSIT_CHOLESKY_U;
     for (int idx = tid; idx < n * n; idx += nt) {
       int i = idx % n, k = idx / n;
-      M[idx] = (P.kind == POSIT_CHOLESKY && k > i) ? pz_zero() : pz_decode(P.A[i + (int64_t)k * P.lda]);
+      bool skip = (lower_only && k > i) || (upper_only && k < i);
+      M[idx] = skip ? pz_zero() : pz_decode(P.A[i + (int64_t)k * P.lda]);
     }
     for (int idx = tid; idx < n * nrhs; idx += nt) {
       int i = idx % n, c = idx / n;
@@ -223,14 +289,17 @@ __global__ void batched_kernel(const posit_problem *__restrict__ probs,
     if (P.kind == POSIT_LU) {
       info = lu_decoded(M, n, P.ipiv, red, sh);
       getrs_decoded(M, n, P.ipiv, X, nrhs);
-    } else {
+    } else if (P.kind == POSIT_CHOLESKY) {
       info = chol_decoded(M, n, sh);
       if (info == 0) potrs_decoded(M, n, X, nrhs, prod);
+    } else {
+      info = chol_decoded_upper(M, n, sh);
+      if (info == 0) potrs_decoded_upper(M, n, X, nrhs);
     }
     __syncthreads();
     for (int idx = tid; idx < n * n; idx += nt) {
       int i = idx % n, k = idx / n;
-      if (P.kind == POSIT_CHOLESKY && k > i) continue;
+      if ((lower_only && k > i) || (upper_only && k < i)) continue;
       P.A[i + (int64_t)k * P.lda] = pz_to_bits(M[idx]);
     }
     if (P.kind == POSIT_LU || info == 0)

@@ -188,20 +188,34 @@ __global__ void __launch_bounds__(PT, 1) panel_kernel(PanelArgs a) {
       if (!grid_barrier(a.bar, G, a.err, a.info)) return;
 
       // every CTA picks the same pivot: largest |a|, then the lowest row
-      if (tid == 0) {
+      // (candidates read in parallel, then a warp / block reduction)
+      {
         uint64_t bk = 0;
         int64_t br = INT64_MAX;
-        int bw = 0;
-        for (unsigned w = 0; w < G; ++w) {
+        for (unsigned w = tid; w < G; w += PT) {
           uint64_t k = __ldcg(&a.cand_key[buf * G + w]);
           int64_t r = __ldcg(&a.cand_row[buf * G + w]);
-          if (r == INT64_MAX) continue;
-          if (k > bk || (k == bk && r < br)) { bk = k; br = r; bw = (int)w; }
+          if (r != INT64_MAX && (k > bk || (k == bk && r < br))) { bk = k; br = r; }
         }
-        s_piv = br;
-        s_flag = bw;
+        for (int off = 16; off > 0; off >>= 1) {
+          uint64_t ok = __shfl_down_sync(0xFFFFFFFFu, bk, off);
+          int64_t orow = __shfl_down_sync(0xFFFFFFFFu, br, off);
+          if (ok > bk || (ok == bk && orow < br)) { bk = ok; br = orow; }
+        }
+        if ((tid & 31) == 0) { red_key[tid >> 5] = bk; red_row[tid >> 5] = br; }
+        __syncthreads();
+        if (tid == 0) {
+          for (int w = 1; w < PT / 32; ++w)
+            if (red_key[w] > bk || (red_key[w] == bk && red_row[w] < br)) {
+              bk = red_key[w];
+              br = red_row[w];
+            }
+          s_piv = br;
+          // the winning CTA is the one whose rows contain br
+          s_flag = (int)((br - a.j) / a.R);
+        }
+        __syncthreads();
       }
-      __syncthreads();
       const int64_t p = s_piv;
       const pz *pv = a.cand_vals + ((size_t)buf * G + s_flag) * jb;
       for (int k = tid; k < jb; k += PT) {
@@ -435,6 +449,7 @@ int device_limits(DeviceLimits &d) {
 }
 
 constexpr int kNB = 256;        // panel width of the timed path
+constexpr int kSub = 32;        // width of the sub-panels factored by the cooperative kernel
 constexpr int kMinRows = 32;    // fewest panel rows per CTA worth a CTA
 
 // Shape of one panel launch: G CTAs of R rows, width jb.
@@ -493,6 +508,12 @@ int laswp(uint32_t *A, int64_t lda, int64_t c0, int64_t c1, int64_t k0, int64_t 
 }  // namespace
 
 // Blocked LU on a caller-provided scratch block (bytes from getrf_scratch_bytes).
+// Two levels: panels of up to kNB columns drive the big trailing Rgemm; each
+// panel is factored in sub-panels of kSub columns by the cooperative kernel,
+// the rest of the panel being brought up to date after each sub-panel by
+// its row swaps, a small unit-lower trsm and a rank-kSub Rgemm.  Every
+// element still receives its updates one column at a time in ascending
+// order, so the factors are those of the unblocked algorithm.
 int getrf_run(int64_t m, int64_t n, uint32_t *A, int64_t lda, int32_t *ipiv, int32_t *info,
               void *scratch, cudaStream_t stream) {
   DeviceLimits d;
@@ -504,18 +525,35 @@ int getrf_run(int64_t m, int64_t n, uint32_t *A, int64_t lda, int32_t *ipiv, int
   if (cudaMemsetAsync(scratch, 0, scratch_bytes(d.sms, kNB), stream) != cudaSuccess)
     return POSIT_ERR_CUDA;
   for (int64_t j = 0; j < mn;) {
-    PanelShape ps = panel_shape(d, m - j, (int)min64(kNB, mn - j));
-    const int jb = ps.jb;
-    PanelArgs pa{};
-    pa.A = A; pa.lda = lda; pa.m = m; pa.j = j; pa.trans = 0; pa.chol = 0;
-    pa.ipiv = ipiv; pa.info = info;
-    pa.bar = s.bar; pa.err = s.err; pa.cand_key = s.cand_key; pa.cand_row = s.cand_row;
-    pa.cand_vals = s.cand_vals; pa.xrow = s.xrow; pa.diag = s.diag;
-    if ((st = launch_panel(pa, ps, stream))) return st;
+    const int64_t jb = min64(kNB, mn - j);
+    for (int64_t sp = j; sp < j + jb;) {
+      PanelShape ps = panel_shape(d, m - sp, (int)min64(kSub, j + jb - sp));
+      const int w = ps.jb;
+      PanelArgs pa{};
+      pa.A = A; pa.lda = lda; pa.m = m; pa.j = sp; pa.trans = 0; pa.chol = 0;
+      pa.ipiv = ipiv; pa.info = info;
+      pa.bar = s.bar; pa.err = s.err; pa.cand_key = s.cand_key; pa.cand_row = s.cand_row;
+      pa.cand_vals = s.cand_vals; pa.xrow = s.xrow; pa.diag = s.diag;
+      if ((st = launch_panel(pa, ps, stream))) return st;
+      // the sub-panel's swaps on the rest of the panel
+      if ((st = laswp(A, lda, j, sp, sp, sp + w, ipiv, stream))) return st;
+      if ((st = laswp(A, lda, sp + w, j + jb, sp, sp + w, ipiv, stream))) return st;
+      if (sp + w < j + jb) {
+        if ((st = trsm_llu(A, lda, sp, w, sp + w, j + jb, stream))) return st;
+        if (sp + w < m) {
+          st = rgemm_launch(false, false, TRI_FULL, m - sp - w, j + jb - sp - w, w, 0xC0000000u,
+                            A + (sp + w) + sp * lda, lda, A + sp + (sp + w) * lda, lda,
+                            PZ_ONE_BITS, A + (sp + w) + (sp + w) * lda, lda, stream);
+          if (st) return st;
+        }
+      }
+      sp += w;
+    }
+    // the panel's swaps on the columns left and right of it
     if ((st = laswp(A, lda, 0, j, j, j + jb, ipiv, stream))) return st;
     if ((st = laswp(A, lda, j + jb, n, j, j + jb, ipiv, stream))) return st;
     if (j + jb < n) {
-      if ((st = trsm_llu(A, lda, j, jb, j + jb, n, stream))) return st;
+      if ((st = trsm_llu(A, lda, j, (int)jb, j + jb, n, stream))) return st;
       if (j + jb < m) {
         st = rgemm_launch(false, false, TRI_FULL, m - j - jb, n - j - jb, jb, 0xC0000000u,
                           A + (j + jb) + j * lda, lda, A + j + (j + jb) * lda, lda,
@@ -543,27 +581,37 @@ int potrf_run(bool upper, int64_t n, uint32_t *A, int64_t lda, int32_t *info, vo
   carve(s, scratch, d.sms, kNB);
   if (cudaMemsetAsync(scratch, 0, scratch_bytes(d.sms, kNB), stream) != cudaSuccess)
     return POSIT_ERR_CUDA;
+  // Panels of up to kNB columns, each factored in kSub-column sub-panels by
+  // the cooperative kernel; the rest of the panel and the trailing triangle
+  // are updated by Rgemm restricted to the factor's triangle.
+  auto tri_update = [&](int64_t t0, int64_t c1, int64_t c0, int64_t kw) -> int {
+    // A(t0.., t0..c1) -= F(t0.., c0..c0+kw) F(t0..c1, c0..c0+kw)^T on the
+    // lower triangle (or the transposed mirror for upper storage)
+    const int64_t rows = n - t0, cols = c1 - t0;
+    if (rows <= 0 || cols <= 0) return POSIT_OK;
+    if (!upper)
+      return rgemm_launch_guarded(false, true, TRI_LOWER, rows, cols, kw, 0xC0000000u,
+                                  A + t0 + c0 * lda, lda, A + t0 + c0 * lda, lda, PZ_ONE_BITS,
+                                  A + t0 + t0 * lda, lda, info, stream);
+    return rgemm_launch_guarded(true, false, TRI_UPPER, cols, rows, kw, 0xC0000000u,
+                                A + c0 + t0 * lda, lda, A + c0 + t0 * lda, lda, PZ_ONE_BITS,
+                                A + t0 + t0 * lda, lda, info, stream);
+  };
   for (int64_t j = 0; j < n;) {
-    PanelShape ps = panel_shape(d, n - j, (int)min64(kNB, n - j));
-    const int jb = ps.jb;
-    PanelArgs pa{};
-    pa.A = A; pa.lda = lda; pa.m = n; pa.j = j; pa.trans = upper ? 1 : 0; pa.chol = 1;
-    pa.ipiv = nullptr; pa.info = info;
-    pa.bar = s.bar; pa.err = s.err; pa.cand_key = s.cand_key; pa.cand_row = s.cand_row;
-    pa.cand_vals = s.cand_vals; pa.xrow = s.xrow; pa.diag = s.diag;
-    if ((st = launch_panel(pa, ps, stream))) return st;
-    if (j + jb < n) {
-      const int64_t t0 = j + jb, nt = n - t0;
-      if (!upper)
-        st = rgemm_launch_guarded(false, true, TRI_LOWER, nt, nt, jb, 0xC0000000u,
-                                  A + t0 + j * lda, lda, A + t0 + j * lda, lda, PZ_ONE_BITS,
-                                  A + t0 + t0 * lda, lda, info, stream);
-      else
-        st = rgemm_launch_guarded(true, false, TRI_UPPER, nt, nt, jb, 0xC0000000u,
-                                  A + j + t0 * lda, lda, A + j + t0 * lda, lda, PZ_ONE_BITS,
-                                  A + t0 + t0 * lda, lda, info, stream);
-      if (st) return st;
+    const int64_t jb = min64(kNB, n - j);
+    for (int64_t sp = j; sp < j + jb;) {
+      PanelShape ps = panel_shape(d, n - sp, (int)min64(kSub, j + jb - sp));
+      const int w = ps.jb;
+      PanelArgs pa{};
+      pa.A = A; pa.lda = lda; pa.m = n; pa.j = sp; pa.trans = upper ? 1 : 0; pa.chol = 1;
+      pa.ipiv = nullptr; pa.info = info;
+      pa.bar = s.bar; pa.err = s.err; pa.cand_key = s.cand_key; pa.cand_row = s.cand_row;
+      pa.cand_vals = s.cand_vals; pa.xrow = s.xrow; pa.diag = s.diag;
+      if ((st = launch_panel(pa, ps, stream))) return st;
+      if ((st = tri_update(sp + w, j + jb, sp, w))) return st;  // rest of the panel
+      sp += w;
     }
+    if ((st = tri_update(j + jb, n, j, jb))) return st;  // trailing triangle
     j += jb;
   }
   return POSIT_OK;

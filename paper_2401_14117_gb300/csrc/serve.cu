@@ -7,8 +7,8 @@
 //   small lane  n <= small_n_max: every admitted, not yet started request is
 //               put into the next persistent batched launch as soon as the
 //               previous small launch has finished (continuous batching);
-//   large lane  n >  small_n_max: one request at a time through the blocked
-//               multi-SM routines.
+//   large lanes n >  small_n_max: through the blocked multi-SM routines, one
+//               request per lane, large_lanes lanes (streams) at once.
 // The caller drives the server: posit_serve_poll retires finished launches
 // (CUDA events, no blocking), frees their memory, admits waiting requests
 // and starts launches.  Results are bit-identical to the single-request
@@ -35,7 +35,13 @@ struct Launch {
   cudaEvent_t done;
   std::vector<int> reqs;
   void *desc;  // device descriptor array (small lane), freed on completion
-  bool small;
+  int lane;    // -1: small lane, else the large lane index
+};
+
+struct Lane {
+  cudaStream_t stream = nullptr;
+  void *scratch = nullptr;
+  bool busy = false;
 };
 
 }  // namespace
@@ -43,15 +49,15 @@ struct Launch {
 
 struct posit_server {
   posit_serve_config cfg;
-  cudaStream_t s_small = nullptr, s_large = nullptr, s_copy = nullptr;
+  cudaStream_t s_small = nullptr, s_copy = nullptr;
+  std::vector<posit::Lane> lanes;  // large lanes
   std::vector<posit::Req> reqs;
   std::vector<int> free_slots;
   std::deque<int> pending, small_ready, large_ready;
   std::vector<posit::Launch> inflight;
-  bool small_busy = false, large_busy = false;
+  bool small_busy = false;
   size_t used = 0;
   void *ws = nullptr;  // batched workspace (small lane)
-  void *scratch = nullptr;  // factorisation / solve scratch (large lane)
   posit_problem *stage = nullptr;  // pinned staging for descriptors
   int64_t stage_cap = 0;
   int64_t admitted = 0, completed = 0, launches = 0, batched = 0, largest = 0;
@@ -103,7 +109,7 @@ int start_small(posit_server *sv, cudaEvent_t ready) {
   const int64_t cnt = std::min<int64_t>((int64_t)sv->small_ready.size(), sv->cfg.max_batch);
   if (cnt <= 0) return POSIT_OK;
   Launch L;
-  L.small = true;
+  L.lane = -1;
   int max_n = 0, max_k = 0;
   for (int64_t i = 0; i < cnt; ++i) {
     int id = sv->small_ready.front();
@@ -144,33 +150,35 @@ int start_small(posit_server *sv, cudaEvent_t ready) {
   return POSIT_OK;
 }
 
-int start_large(posit_server *sv, cudaEvent_t ready) {
+int start_large(posit_server *sv, int lane, cudaEvent_t ready) {
   if (sv->large_ready.empty()) return POSIT_OK;
   int id = sv->large_ready.front();
   sv->large_ready.pop_front();
   const Req &q = sv->reqs[id];
-  if (cudaStreamWaitEvent(sv->s_large, ready, 0) != cudaSuccess) return POSIT_ERR_CUDA;
+  Lane &ln = sv->lanes[lane];
+  if (cudaStreamWaitEvent(ln.stream, ready, 0) != cudaSuccess) return POSIT_ERR_CUDA;
   int st;
   const int64_t n = q.r.n, k = q.r.nrhs;
   if (q.r.kind == POSIT_LU) {
-    st = getrf_run(n, n, q.dA, n, q.dipiv, q.dinfo, sv->scratch, sv->s_large);
-    if (!st) st = getrs_run(false, n, k, q.dA, n, q.dipiv, q.dB, n, sv->scratch, sv->s_large);
+    st = getrf_run(n, n, q.dA, n, q.dipiv, q.dinfo, ln.scratch, ln.stream);
+    if (!st) st = getrs_run(false, n, k, q.dA, n, q.dipiv, q.dB, n, ln.scratch, ln.stream);
   } else {
-    st = potrf_run(false, n, q.dA, n, q.dinfo, sv->scratch, sv->s_large);
+    const bool upper = q.r.kind == POSIT_CHOLESKY_U;
+    st = potrf_run(upper, n, q.dA, n, q.dinfo, ln.scratch, ln.stream);
     // the solve is skipped on the device when info != 0 (B then keeps b)
-    if (!st) st = potrs_run_guarded(false, n, k, q.dA, n, q.dB, n, q.dinfo, sv->scratch, sv->s_large);
+    if (!st) st = potrs_run_guarded(upper, n, k, q.dA, n, q.dB, n, q.dinfo, ln.scratch, ln.stream);
   }
   if (st) return st;
-  if ((st = finish_copies(sv, q, sv->s_large))) return st;
+  if ((st = finish_copies(sv, q, ln.stream))) return st;
   Launch L;
-  L.small = false;
+  L.lane = lane;
   L.desc = nullptr;
   L.reqs.push_back(id);
   if (cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventRecord(L.done, sv->s_large) != cudaSuccess)
+      cudaEventRecord(L.done, ln.stream) != cudaSuccess)
     return POSIT_ERR_CUDA;
   sv->inflight.push_back(L);
-  sv->large_busy = true;
+  ln.busy = true;
   sv->launches++;
   return POSIT_OK;
 }
@@ -184,20 +192,27 @@ extern "C" int posit_serve_open(const posit_serve_config *cfg, posit_server **ou
   if (!cfg) return -1;
   if (!out) return -2;
   if (cfg->budget_bytes <= 0 || cfg->small_n_max < 1 || cfg->small_n_max > 46340 ||
-      cfg->max_batch < 1 || cfg->max_nrhs < 1)
+      cfg->max_batch < 1 || cfg->max_nrhs < 1 || cfg->large_lanes < 0 || cfg->large_lanes > 64)
     return -1;
   posit_server *sv = new (std::nothrow) posit_server();
   if (!sv) return POSIT_ERR_ALLOC;
   sv->cfg = *cfg;
+  if (sv->cfg.large_lanes == 0) sv->cfg.large_lanes = 16;
   int st = POSIT_OK;
   if (cudaStreamCreateWithFlags(&sv->s_small, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&sv->s_large, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&sv->s_copy, cudaStreamNonBlocking) != cudaSuccess)
     st = POSIT_ERR_CUDA;
   size_t wsb = batched_workspace_bytes(cfg->small_n_max, cfg->max_nrhs, cfg->plan);
   size_t scr = std::max(getrf_scratch_bytes(), solve_scratch_bytes());
   if (!st && (!wsb || cudaMalloc(&sv->ws, wsb) != cudaSuccess)) st = POSIT_ERR_ALLOC;
-  if (!st && cudaMalloc(&sv->scratch, scr) != cudaSuccess) st = POSIT_ERR_ALLOC;
+  sv->lanes.resize(sv->cfg.large_lanes);
+  for (auto &ln : sv->lanes) {
+    if (st) break;
+    if (cudaStreamCreateWithFlags(&ln.stream, cudaStreamNonBlocking) != cudaSuccess)
+      st = POSIT_ERR_CUDA;
+    else if (cudaMalloc(&ln.scratch, scr) != cudaSuccess)
+      st = POSIT_ERR_ALLOC;
+  }
   sv->stage_cap = cfg->max_batch;
   if (!st && cudaMallocHost(&sv->stage, sizeof(posit_problem) * cfg->max_batch) != cudaSuccess)
     st = POSIT_ERR_ALLOC;
@@ -212,7 +227,8 @@ extern "C" int posit_serve_open(const posit_serve_config *cfg, posit_server **ou
 
 extern "C" int posit_serve_submit(posit_server *sv, const posit_request *req) {
   if (!sv) return -1;
-  if (!req || (req->kind != POSIT_LU && req->kind != POSIT_CHOLESKY) || req->n < 1 ||
+  if (!req || (req->kind != POSIT_LU && req->kind != POSIT_CHOLESKY &&
+               req->kind != POSIT_CHOLESKY_U) || req->n < 1 ||
       req->nrhs < 1 || req->nrhs > sv->cfg.max_nrhs || !req->A || !req->B || !req->X || !req->info)
     return -2;
   posit::Req q;
@@ -247,16 +263,17 @@ extern "C" int posit_serve_poll(posit_server *sv, uint64_t *done_tags, int64_t m
     if (e == cudaErrorNotReady) { ++i; continue; }
     if (e != cudaSuccess) return POSIT_ERR_CUDA;
     cudaEventDestroy(L.done);
+    cudaStream_t ls = L.lane < 0 ? sv->s_small : sv->lanes[L.lane].stream;
     for (int id : L.reqs) {
       Req &q = sv->reqs[id];
-      cudaFreeAsync(q.dev, L.small ? sv->s_small : sv->s_large);
+      cudaFreeAsync(q.dev, ls);
       sv->used -= q.bytes;
       done_tags[(*n_done)++] = q.r.tag;
       sv->free_slots.push_back(id);
       sv->completed++;
     }
     if (L.desc) cudaFreeAsync(L.desc, sv->s_small);
-    if (L.small) sv->small_busy = false; else sv->large_busy = false;
+    if (L.lane < 0) sv->small_busy = false; else sv->lanes[L.lane].busy = false;
     sv->inflight.erase(sv->inflight.begin() + i);
   }
   // 2. admit waiting requests in arrival order while they fit the budget
@@ -272,15 +289,20 @@ extern "C" int posit_serve_poll(posit_server *sv, uint64_t *done_tags, int64_t m
     any = true;
   }
   // 3. start launches on idle lanes; they wait for the admitted copies
-  cudaEvent_t ready = nullptr;
-  if ((any || !sv->small_busy || !sv->large_busy) &&
-      (!sv->small_ready.empty() || !sv->large_ready.empty())) {
+  (void)any;
+  bool small_go = !sv->small_busy && !sv->small_ready.empty();
+  bool large_go = false;
+  for (auto &ln : sv->lanes) large_go |= !ln.busy;
+  large_go &= !sv->large_ready.empty();
+  if (small_go || large_go) {
+    cudaEvent_t ready = nullptr;
     if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventRecord(ready, sv->s_copy) != cudaSuccess)
       return POSIT_ERR_CUDA;
     int st = POSIT_OK;
-    if (!sv->small_busy && !sv->small_ready.empty()) st = start_small(sv, ready);
-    if (!st && !sv->large_busy && !sv->large_ready.empty()) st = start_large(sv, ready);
+    if (small_go) st = start_small(sv, ready);
+    for (size_t l = 0; !st && l < sv->lanes.size() && !sv->large_ready.empty(); ++l)
+      if (!sv->lanes[l].busy) st = start_large(sv, (int)l, ready);
     cudaEventDestroy(ready);
     if (st) return st;
   }
@@ -304,7 +326,8 @@ extern "C" int posit_serve_stats(const posit_server *sv, posit_serve_stats_t *st
 extern "C" int posit_serve_close(posit_server *sv) {
   if (!sv) return -1;
   if (sv->s_small) cudaStreamSynchronize(sv->s_small);
-  if (sv->s_large) cudaStreamSynchronize(sv->s_large);
+  for (auto &ln : sv->lanes)
+    if (ln.stream) cudaStreamSynchronize(ln.stream);
   if (sv->s_copy) cudaStreamSynchronize(sv->s_copy);
   for (auto &L : sv->inflight) {
     cudaEventDestroy(L.done);
@@ -314,10 +337,12 @@ extern "C" int posit_serve_close(posit_server *sv) {
   for (int id : sv->small_ready) cudaFree(sv->reqs[id].dev);
   for (int id : sv->large_ready) cudaFree(sv->reqs[id].dev);
   if (sv->ws) cudaFree(sv->ws);
-  if (sv->scratch) cudaFree(sv->scratch);
+  for (auto &ln : sv->lanes) {
+    if (ln.scratch) cudaFree(ln.scratch);
+    if (ln.stream) cudaStreamDestroy(ln.stream);
+  }
   if (sv->stage) cudaFreeHost(sv->stage);
   if (sv->s_small) cudaStreamDestroy(sv->s_small);
-  if (sv->s_large) cudaStreamDestroy(sv->s_large);
   if (sv->s_copy) cudaStreamDestroy(sv->s_copy);
   delete sv;
   return POSIT_OK;

@@ -179,13 +179,16 @@ __global__ void __launch_bounds__(ST, 1) trsv_wave_kernel(TriArgs a) {
 
 // x_i = (b_i - sum_{k>i, ascending} a(k, i) x_k) / a(i, i), i = n-1 .. 0,
 // for one right-hand side per CTA (column blockIdx.x of B).  a(k, i) is
-// A[k + i*lda] (column i below the diagonal).
+// A[k + i*lda] (column i below the diagonal).  The products of a row are
+// formed in parallel (the next chunk while the current one is consumed) and
+// stored negated; one thread runs the chain of rounded additions, the only
+// serial part, with the NaR-free fast add (a NaR product or b_i makes x_i
+// NaR; that test is off the chain's dependency path).
 __global__ void __launch_bounds__(ST) trsv_dot_backward_kernel(const uint32_t *__restrict__ A,
                                                                 int64_t lda, uint32_t *B,
                                                                 int64_t ldb, int64_t n, int unit,
                                                                 const int32_t *abort_flag) {
-  __shared__ pz prod[ST];
-  __shared__ pz acc_s;
+  __shared__ pz prod[2][ST];
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pz *x = reinterpret_cast<pz *>(smem_raw);  // [n] the right-hand side / solution
   uint32_t *b = B + (int64_t)blockIdx.x * ldb;
@@ -195,21 +198,37 @@ __global__ void __launch_bounds__(ST) trsv_dot_backward_kernel(const uint32_t *_
   __syncthreads();
   for (int64_t i = n - 1; i >= 0; --i) {
     const uint32_t *col = A + i * lda;
-    if (tid == 0) acc_s = x[i];
+    {
+      int64_t k = i + 1 + tid;
+      if (k < n) {
+        pz p = pz_mul(pz_decode(col[k]), x[k]);
+        prod[0][tid] = pz{p.s, p.m ^ 0x80000000u};
+      }
+    }
+    __syncthreads();
+    pz acc = x[i];
+    bool nar = pz_is_nar(acc);
+    int buf = 0;
     for (int64_t k0 = i + 1; k0 < n; k0 += ST) {
-      int64_t k = k0 + tid;
-      if (k < n) prod[tid] = pz_mul(pz_decode(col[k]), x[k]);
-      __syncthreads();
+      int64_t kn = k0 + ST + tid;
+      if (kn < n) {
+        pz p = pz_mul(pz_decode(col[kn]), x[kn]);
+        prod[buf ^ 1][tid] = pz{p.s, p.m ^ 0x80000000u};
+      }
       if (tid == 0) {
-        pz acc = acc_s;
-        int cnt = (int)min64(ST, n - k0);
-        for (int t = 0; t < cnt; ++t) acc = pz_sub(acc, prod[t]);
-        acc_s = acc;
+        const int cnt = (int)min64(ST, n - k0);
+        const pz *pr = prod[buf];
+        for (int t = 0; t < cnt; ++t) {
+          pz p = pr[t];
+          nar |= p.s >= PZ_NAR_T;
+          acc = pz_add_fast(acc, p);
+        }
       }
       __syncthreads();
+      buf ^= 1;
     }
     if (tid == 0) {
-      pz v = acc_s;
+      pz v = nar ? pz_nar() : pz_canon(acc, false);
       if (!unit) v = pz_div(v, pz_decode(col[i]));
       x[i] = v;
     }

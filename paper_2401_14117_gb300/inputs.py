@@ -12,6 +12,7 @@ matrices with mean 0 and a chosen sigma, Sec. 4 and Sec. 5):
               (long regimes, |x| up to 1e4)
   * normal:   N(0, sigma^2), the paper's generator (Sec. 4.2, Sec. 5.1)
   * spd:      A = G G^T / n + I with G standard normal, in FP64
+  * spd_sigma: sigma^2 (G G^T / n + I), the SPD matrices of the sigma sweep
   * rhs:      b = A x_sol with x_sol = 1/sqrt(n) in every entry, in FP64
               (Sec. 5.1, error study)
 """
@@ -50,6 +51,13 @@ def spd(n: int, seed: int, device=None):
     Gt = torch.from_numpy(G).to(device)
     A = Gt @ Gt.T / n + torch.eye(n, dtype=torch.float64, device=device)
     return A.cpu().numpy()
+
+
+def spd_sigma(n: int, seed: int, sigma: float, device=None):
+    """sigma^2 (G G^T / n + I): the SPD recipe with entries of size sigma^2,
+    as the paper's X^T X with X ~ N(0, sigma^2) has (Sec. 5.1), while the
+    condition number stays that of G G^T / n + I."""
+    return spd(n, seed, device) * (sigma * sigma)
 
 
 def rhs(A64: np.ndarray) -> np.ndarray:

@@ -25,12 +25,13 @@ from . import binding, inputs
 class Pool:
     """Seeded problems in page-locked host memory (posit words)."""
 
-    def __init__(self, size, n_lo, n_hi, nrhs_max, seed, lu_fraction=0.5, device=None):
+    def __init__(self, size, n_lo, n_hi, nrhs_max, seed, lu_fraction=0.5, device=None,
+                 cholesky_kind=binding.POSIT_CHOLESKY):
         dev = device or torch.device("cuda", torch.cuda.current_device())
         g = np.random.default_rng(seed)
         self.ns = np.rint(np.exp(g.uniform(math.log(n_lo), math.log(n_hi), size))).astype(np.int64)
         self.kinds = np.where(g.random(size) < lu_fraction, binding.POSIT_LU,
-                              binding.POSIT_CHOLESKY).astype(np.int32)
+                              cholesky_kind).astype(np.int32)
         self.nrhs = g.integers(1, nrhs_max + 1, size).astype(np.int64)
         self.A, self.B = [], []
         for i in range(size):
@@ -61,9 +62,9 @@ class Pool:
 
 
 def default_config(budget_gb=40.0, small_n_max=512, max_batch=1024, max_nrhs=8,
-                   plan=(256, 1, 200 * 1024)):
+                   plan=(512, 4, 48 * 1024), large_lanes=16):
     return binding.posit_serve_config(int(budget_gb * 2 ** 30), small_n_max, max_batch,
-                                      max_nrhs, 0, binding.posit_plan(*plan, 0))
+                                      max_nrhs, large_lanes, binding.posit_plan(*plan, 0))
 
 
 def run(pool, arrival_times, pool_index, cfg, duration, max_outstanding=256, capture=None,

@@ -11,7 +11,7 @@ from paper_2401_14117_gb300.batch import ProblemSet, plan_of
 
 pytestmark = pytest.mark.gpu
 
-L, C = binding.POSIT_LU, binding.POSIT_CHOLESKY
+L, C, CU = binding.POSIT_LU, binding.POSIT_CHOLESKY, binding.POSIT_CHOLESKY_U
 
 
 def make_set(kinds, ns, nrhs, seed):
@@ -33,8 +33,9 @@ def expected(kind, A, B):
         F, ipiv, info = oracle.rgetrf(A)
         X = oracle.rgetrs(F, ipiv, B)
         return F, X, ipiv, info
-    F, info = oracle.rpotrf(A, uplo="L")
-    X = oracle.rpotrs(F, B, uplo="L") if info == 0 else B
+    uplo = "U" if kind == CU else "L"
+    F, info = oracle.rpotrf(A, uplo=uplo)
+    X = oracle.rpotrs(F, B, uplo=uplo) if info == 0 else B
     return F, X, None, info
 
 
@@ -48,9 +49,12 @@ def check(ps, host, idxs=None):
         if ps.kinds[i] == L:
             assert np.array_equal(gF, F), i
             assert np.array_equal(gp, ipiv), i
-        else:
+        elif ps.kinds[i] == C:
             assert np.array_equal(np.tril(gF), np.tril(F)), i
             assert np.array_equal(np.triu(gF, 1), np.triu(A, 1)), i  # upper untouched
+        else:
+            assert np.array_equal(np.triu(gF), np.triu(F)), i
+            assert np.array_equal(np.tril(gF, -1), np.tril(A, -1)), i  # lower untouched
         assert np.array_equal(gX, X.reshape(n, -1)), i
 
 
@@ -62,7 +66,7 @@ def test_batched_matches_oracle(plan):
     rng = np.random.default_rng(3)
     count = 40
     ns = np.concatenate([[1, 2, 3, 200, 300], rng.integers(4, 140, count - 5)])
-    kinds = np.array([L if i % 2 == 0 else C for i in range(count)], np.int32)
+    kinds = np.array([(L, C, CU)[i % 3] for i in range(count)], np.int32)
     nrhs = rng.integers(1, 4, count)
     ps, host = make_set(kinds, ns, nrhs, 100)
     ps.run(plan_of(*plan))

@@ -22,10 +22,11 @@ def alone(pool, i):
         binding.posit_rgetrf(n, n, A, n, ipiv, info)
         binding.posit_rgetrs("N", n, r, A, n, ipiv, B, n)
     else:
-        binding.posit_rpotrf("L", n, A, n, info)
+        uplo = "U" if pool.kinds[i] == binding.POSIT_CHOLESKY_U else "L"
+        binding.posit_rpotrf(uplo, n, A, n, info)
         torch.cuda.synchronize()
         if int(info.item()) == 0:
-            binding.posit_rpotrs("L", n, r, A, n, B, n)
+            binding.posit_rpotrs(uplo, n, r, A, n, B, n)
     torch.cuda.synchronize()
     return B.cpu().numpy().view(np.uint32).reshape(-1), int(info.item())
 
@@ -38,14 +39,17 @@ def oracle_solution(pool, i):
         F, ipiv, info = oracle.rgetrf(A)
         X = oracle.rgetrs(F, ipiv, B)
     else:
-        F, info = oracle.rpotrf(A)
-        X = oracle.rpotrs(F, B) if info == 0 else B
+        uplo = "U" if pool.kinds[i] == binding.POSIT_CHOLESKY_U else "L"
+        F, info = oracle.rpotrf(A, uplo=uplo)
+        X = oracle.rpotrs(F, B, uplo=uplo) if info == 0 else B
     return np.asfortranarray(X).ravel(order="F"), info
 
 
-@pytest.mark.parametrize("small_n_max", [96, 512])
-def test_served_results_equal_alone_and_oracle(small_n_max):
-    pool = serving.Pool(20, 16, 700, 4, seed=77)
+@pytest.mark.parametrize("small_n_max,chol", [(96, binding.POSIT_CHOLESKY),
+                                              (512, binding.POSIT_CHOLESKY),
+                                              (256, binding.POSIT_CHOLESKY_U)])
+def test_served_results_equal_alone_and_oracle(small_n_max, chol):
+    pool = serving.Pool(20, 16, 700, 4, seed=77, cholesky_kind=chol)
     t, idx = serving.arrivals(400.0, 1.5, pool.size, seed=78)
     cfg = serving.default_config(budget_gb=2.0, small_n_max=small_n_max, max_batch=64)
     res = serving.run(pool, t, idx, cfg, duration=1.5, max_outstanding=64,
