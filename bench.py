@@ -57,6 +57,16 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the other workloads (LU/Cholesky/solves, batched, serving)")
+    p.add_argument("--serve-seconds", type=float, default=10.0)
+    p.add_argument("--serve-rate-sustained", type=float, default=60.0,
+                   help="arrival rate (requests/s) of the sustainable serving run")
+    p.add_argument("--extras", default="all",
+                   help="comma list of extra workloads: elementwise, rgemm, ksweep, sigma, "
+                        "factor, power, accuracy, batched, serving; or all")
+    p.add_argument("--ew-size", type=int, default=1 << 24,
+                   help="elements per element-wise launch")
     return p.parse_args()
 
 
@@ -65,6 +75,27 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def rank_seed(rank):
+    """Each rank multiplies its own seeded matrices (independent problems)."""
+    from paper_2401_14117_gb300 import inputs
+    return inputs.SEED_BASE + 1 + 1000 * rank
+
+
+def max_over_ranks(x, world, device):
+    """The largest x over all ranks (x itself on one rank)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gflops(ops_per_rank_step, world, steps, t_max_ms):
+    """Whole-job rate: the work of every rank over the slowest rank's time."""
+    return ops_per_rank_step * world * steps / (t_max_ms / 1e3) / 1e9
 
 
 def workload_name(m, n, k):
@@ -171,7 +202,7 @@ class ClockSampler:
                 self.out, _ = self.proc.communicate()
 
     def summary(self):
-        sm, mx, reasons = [], [], set()
+        sm, mx, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in (self.out or "").splitlines():
             f = [x.strip() for x in line.split(",")]
@@ -182,13 +213,19 @@ class ClockSampler:
                 mx.append(float(f[1]))
             except ValueError:
                 continue
+            try:
+                pw.append(float(f[2]))
+            except ValueError:
+                pass
             for nm, v in zip(names, f[4:8]):
                 if v.lower() == "active":
                     reasons.add(nm)
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
+                    "power_w": None}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w": statistics.median(pw) if pw else None}
 
 
 # ------------------------------------------------------------------ ours
@@ -206,7 +243,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=dev)
     m = n = args.size
     k = args.k or args.size
-    seed = inputs.SEED_BASE + 1 + 1000 * rank
+    seed = rank_seed(rank)
     stream = torch.cuda.current_stream()
 
     def dev_words(shape, s):
@@ -256,13 +293,9 @@ def run_ours(args):
     clocks = clk.summary()
     kernel_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
     total_ms = total0.elapsed_time(total1)
-    t_local = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    t_max_ms = float(t_local.item())
+    t_max_ms = max_over_ranks(total_ms, world, dev)
     ops = 2.0 * m * n * k
-    value = ops * world * args.steps / (t_max_ms / 1e3) / 1e9
+    value = job_gflops(ops, world, args.steps, t_max_ms)
     launch_ms = statistics.mean(kernel_ms)
 
     # ---------------------------------------------------------- e2e
@@ -289,11 +322,8 @@ def run_ours(args):
         for _ in range(args.steps):
             e2e_step()
         barrier()
-        t_e2e = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
-        if world > 1:
-            import torch.distributed as dist
-            dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
-        e2e = {"value": ops * world * args.steps / float(t_e2e.item()) / 1e9, "unit": UNIT,
+        t_e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3, world, dev)
+        e2e = {"value": job_gflops(ops, world, args.steps, t_e2e_ms), "unit": UNIT,
                "h2d_bytes_per_step": 4 * (m * k + k * n), "d2h_bytes_per_step": 4 * m * n}
         del eA, eB, eC
 
@@ -316,6 +346,10 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "posit32", "data": "synthetic", "config": config(m, n, k),
             "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks, "roofline": roofline}
+    if rank == 0 and world == 1 and not args.no_extras:
+        args.square_ms = launch_ms if m == n == k == 8192 else None
+        line["extras"] = extras(args, dev, stream)
+        line["extras"]["headline_power_w"] = clocks.get("power_w")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, sample = oracle_sample_rate(m, n, k, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores,
@@ -325,6 +359,319 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ extras
+def _time_ms(fn, stream, reps=2, setup=None):
+    import torch
+    best = float("inf")
+    for _ in range(reps):
+        if setup is not None:
+            setup()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def extras(args, dev, stream):
+    """The other workloads of the hot path, each timed with CUDA events on
+    its launching stream (inputs resident on the device)."""
+    import numpy as np
+    import torch
+
+    from paper_2401_14117_gb300 import accuracy, autotune, binding, inputs, serving
+    from paper_2401_14117_gb300.batch import ProblemSet, plan_of
+    out = {}
+    sections = set(args.extras.split(","))
+
+    def want(name):
+        return "all" in sections or name in sections
+
+    def words(shape, seed, spd=False, sigma=None):
+        if spd:
+            x = torch.from_numpy(inputs.spd(shape[0], seed, device=dev)).to(dev)
+        elif sigma is not None:
+            x = torch.from_numpy(inputs.normal(shape, seed, sigma)).to(dev)
+        else:
+            x = torch.from_numpy(inputs.uniform(shape, seed)).to(dev)
+        w = torch.empty(x.shape, dtype=torch.int32, device=dev)
+        binding.posit_from_double(x.T.contiguous() if spd else x, w, x.numel(), stream)
+        return w
+
+    # element-wise Add/Mul/Div/Sqrt over the argument ranges of Sec. 4.2
+    # (Table tabrandom): ns per op, and the paper's "per CUDA core" figure
+    # (time x cores / S, with 152 SMs x 128 cores)
+    if want("elementwise"):
+        ranges = {"I0 [1,2)": (1.0, 2.0), "I1 [1e-38,1e-30)": (1e-38, 1e-30),
+                  "I2 [1e30,1e38)": (1e30, 1e38), "I3 [1e-15,1e-14)": (1e-15, 1e-14),
+                  "I4 [1e14,1e15)": (1e14, 1e15)}
+        S = args.ew_size
+        ew = {}
+        for r_i, (name, (lo, hi)) in enumerate(ranges.items()):
+            p = torch.from_numpy(inputs.uniform(S, inputs.SEED_BASE + 40 + 2 * r_i, lo, hi)).to(dev)
+            q = torch.from_numpy(inputs.uniform(S, inputs.SEED_BASE + 41 + 2 * r_i, lo, hi)).to(dev)
+            pw = torch.empty(S, dtype=torch.int32, device=dev)
+            qw = torch.empty(S, dtype=torch.int32, device=dev)
+            rw = torch.empty(S, dtype=torch.int32, device=dev)
+            binding.posit_from_double(p, pw, S, stream)
+            binding.posit_from_double(q, qw, S, stream)
+            row = {}
+            for op, code in (("add", 0), ("mul", 2), ("div", 3), ("sqrt", 4)):
+                ms = _time_ms(lambda: binding.posit_elementwise(code, pw, qw, rw, S, stream), stream,
+                              reps=3)
+                nbytes = (8 if op == "sqrt" else 12) * S
+                row[op] = {"ns_per_op": ms * 1e6 / S, "ns_per_op_per_core": ms * 1e6 / S * 152 * 128,
+                           "GB/s": nbytes / (ms / 1e3) / 1e9}
+            ew[name] = row
+            del p, q, pw, qw, rw
+        ew["note"] = (f"{S} elements per launch, operands uniform in the range; "
+                      "GB/s counts 4-byte words read and written once")
+        out["elementwise"] = ew
+
+    # Rgemm: the other square sizes and the trailing-update shape
+    if want("rgemm"):
+        gemm = {}
+        for (m, n, k, name) in ((1024, 1024, 1024, "1024^3"), (4096, 4096, 4096, "4096^3"),
+                                (8192, 8192, 256, "8192x8192x256 alpha=-1 beta=1")):
+            A, B, C = words((k, m), 11), words((n, k), 12), words((n, m), 13)
+            alpha, beta = (0xC0000000, ONE) if k == 256 else (ONE, 0)
+            ms = _time_ms(lambda: binding.posit_rgemm("N", "N", m, n, k, alpha, A, m, B, k, beta,
+                                                      C, m, stream), stream, reps=3)
+            gemm[name] = {"ms": ms, "gflops": 2.0 * m * n * k / (ms / 1e3) / 1e9}
+            del A, B, C
+        # the two input sets at 4096^3, with the binary32 GEMM of the same
+        # words (TF32 off) and the accuracy of both against FP64
+        m = 4096
+        prev_tf32 = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = False
+        for label, gen in (("uniform", inputs.uniform), ("scaled", inputs.scaled)):
+            A, B = torch.empty((m, m), dtype=torch.int32, device=dev), torch.empty(
+                (m, m), dtype=torch.int32, device=dev)
+            binding.posit_from_double(torch.from_numpy(gen((m, m), 17)).to(dev), A, m * m, stream)
+            binding.posit_from_double(torch.from_numpy(gen((m, m), 18)).to(dev), B, m * m, stream)
+            C = torch.empty_like(A)
+            ms = _time_ms(lambda: binding.posit_rgemm("N", "N", m, m, m, ONE, A, m, B, m, 0, C, m,
+                                                      stream), stream, reps=2)
+            a64, b64, c64p = (torch.empty((m, m), dtype=torch.float64, device=dev)
+                              for _ in range(3))
+            binding.posit_to_double(A, a64, m * m, stream)
+            binding.posit_to_double(B, b64, m * m, stream)
+            binding.posit_to_double(C, c64p, m * m, stream)
+            # column-major words: the row-major tensors hold A^T, B^T and C^T
+            ref = b64 @ a64  # (A B)^T in FP64
+            a32, b32 = a64.float(), b64.float()
+            ms32 = _time_ms(lambda: torch.matmul(b32, a32), torch.cuda.current_stream(), reps=2)
+            c32 = torch.matmul(b32, a32).double()
+            nref = torch.linalg.vector_norm(ref)
+            gemm[f"4096^3 {label}"] = {
+                "ms": ms, "gflops": 2.0 * m ** 3 / (ms / 1e3) / 1e9,
+                "rel_error_fro": float(torch.linalg.vector_norm(c64p - ref) / nref),
+                "binary32_ms": ms32,
+                "binary32_rel_error_fro": float(torch.linalg.vector_norm(c32 - ref) / nref)}
+            del A, B, C, a64, b64, c64p, ref, a32, b32, c32
+        torch.backends.cuda.matmul.allow_tf32 = prev_tf32
+        gemm["note"] = ("scaled: uniform [-1,1] x 10^u, u ~ U[-4,4] per entry; errors are "
+                        "||C - C_fp64|| / ||C_fp64|| (Frobenius) on the same posit inputs; "
+                        "binary32 = torch.matmul in FP32 with TF32 off")
+        out["rgemm"] = gemm
+
+    # trailing-update K sweep (Sec. 5.3, Fig. gemm_trailing): C <- C - A B with
+    # M = N = 8192, relative to the square 8192^3 rate of the headline
+    if want("ksweep"):
+        m = n = 8192
+        sq_ms = getattr(args, "square_ms", None)
+        sq = 2.0 * m * n * m / (sq_ms / 1e3) / 1e9 if sq_ms else None
+        ksw = {}
+        for k in (32, 64, 128, 256, 512, 1024, 2048):
+            A, B, C = words((k, m), 14), words((n, k), 15), words((n, m), 16)
+            ms = _time_ms(lambda: binding.posit_rgemm("N", "N", m, n, k, 0xC0000000, A, m, B, k, ONE,
+                                                      C, m, stream), stream, reps=3)
+            gf = 2.0 * m * n * k / (ms / 1e3) / 1e9
+            ksw[str(k)] = {"ms": ms, "gflops": gf, "relative_to_square": gf / sq if sq else None}
+            del A, B, C
+        out["trailing_k_sweep"] = ksw
+
+    # sigma sweep (Sec. 4.3 Fig. gemm_v100, Sec. 5.1 Fig. cho_err): normal
+    # N(0, sigma^2) inputs; Rgemm 4096^3 rate and the LU / Cholesky accuracy
+    # advantage over binary32 at n = 2048
+    if want("sigma"):
+        sig = {}
+        for s_i, sigma in enumerate((1e-2, 1.0, 1e2, 1e4, 1e6)):
+            m = 4096
+            A, B, C = (words((m, m), 60 + 3 * s_i, sigma=sigma), words((m, m), 61 + 3 * s_i, sigma=sigma),
+                       torch.empty((m, m), dtype=torch.int32, device=dev))
+            ms = _time_ms(lambda: binding.posit_rgemm("N", "N", m, m, m, ONE, A, m, B, m, 0, C, m,
+                                                      stream), stream, reps=2)
+            del A, B, C
+            A64 = torch.from_numpy(inputs.normal((2048, 2048), 70 + s_i, sigma)).to(dev)
+            lu = accuracy.solve_accuracy(A64, "lu")
+            S64 = torch.from_numpy(inputs.spd_sigma(2048, 80 + s_i, sigma, device=dev)).to(dev)
+            ch = accuracy.solve_accuracy(S64, "cholesky")
+            del A64, S64
+            sig[f"{sigma:g}"] = {"rgemm_4096_gflops": 2.0 * m ** 3 / (ms / 1e3) / 1e9,
+                                 "lu_log10_e32_over_eposit": lu["log10_e32_over_eposit"],
+                                 "cholesky_log10_e32_over_eposit": ch["log10_e32_over_eposit"],
+                                 "lu_backward_error": [lu["posit"]["backward_error_2"],
+                                                       lu["binary32"]["backward_error_2"]],
+                                 "cholesky_backward_error": [ch["posit"]["backward_error_2"],
+                                                             ch["binary32"]["backward_error_2"]],
+                                 "info": [lu["info"], ch["info"]]}
+        sig["note"] = ("LU: A ~ N(0, sigma^2); Cholesky: A = sigma^2 (G G^T / n + I); "
+                       "backward errors listed [posit, binary32]")
+        out["sigma_sweep"] = sig
+
+    # Rgetrf / Rpotrf / Rgetrs / Rpotrs at n = 8192, nb = 256 (1 RHS)
+    if want("factor"):
+        n = 8192
+        fac = {}
+        A0 = words((n, n), 21)
+        S0 = words((n, n), 22, spd=True)
+        b0 = words((1, n), 23)
+        A = torch.empty_like(A0)
+        S = torch.empty_like(S0)
+        ipiv = torch.zeros(n, dtype=torch.int32, device=dev)
+        info = torch.zeros(1, dtype=torch.int32, device=dev)
+        ms = _time_ms(lambda: binding.posit_rgetrf(n, n, A, n, ipiv, info, stream), stream,
+                      setup=lambda: A.copy_(A0))
+        fac["rgetrf_8192"] = {"ms": ms, "gflops": 2 * n ** 3 / 3 / (ms / 1e3) / 1e9,
+                              "info": int(info.item())}
+        ms = _time_ms(lambda: binding.posit_rpotrf("L", n, S, n, info, stream), stream,
+                      setup=lambda: S.copy_(S0))
+        fac["rpotrf_8192"] = {"ms": ms, "gflops": n ** 3 / 3 / (ms / 1e3) / 1e9,
+                              "info": int(info.item())}
+        b = torch.empty_like(b0)
+        ms = _time_ms(lambda: binding.posit_rgetrs("N", n, 1, A, n, ipiv, b, n, stream), stream,
+                      setup=lambda: b.copy_(b0))
+        fac["rgetrs_8192"] = {"ms": ms, "GB/s (factor read once)": 4.0 * n * n / (ms / 1e3) / 1e9}
+        ms = _time_ms(lambda: binding.posit_rpotrs("L", n, 1, S, n, b, n, stream), stream, reps=1,
+                      setup=lambda: b.copy_(b0))
+        fac["rpotrs_8192"] = {"ms": ms, "note": "dot-form L^T solve: one serial chain of "
+                                                "n(n-1)/2 rounded additions"}
+        out["factor"] = fac
+        del A0, S0, A, S
+
+    # board power during back-to-back Rgetrf 8192 (Sec. 5.3, Table PowerE):
+    # NVML board power sampled every 200 ms, read only
+    if want("power"):
+        n = 8192
+        A0 = words((n, n), 21)
+        A = torch.empty_like(A0)
+        ipiv = torch.zeros(n, dtype=torch.int32, device=dev)
+        info = torch.zeros(1, dtype=torch.int32, device=dev)
+        ms = _time_ms(lambda: binding.posit_rgetrf(n, n, A, n, ipiv, info, stream), stream,
+                      reps=1, setup=lambda: A.copy_(A0))
+        reps = max(3, int(4000.0 / ms))
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                A.copy_(A0)
+                binding.posit_rgetrf(n, n, A, n, ipiv, info, stream)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+        pc = clk.summary()
+        gf = reps * 2 * n ** 3 / 3 / wall / 1e9
+        out["power"] = {"workload": f"{reps} x Rgetrf 8192 back to back (with the input copy)",
+                        "gflops": gf, "board_power_w": pc["power_w"], "sm_mhz": pc["sm_mhz"],
+                        "gflops_per_w": gf / pc["power_w"] if pc["power_w"] else None,
+                        "reasons": pc["reasons"], "samples": pc["samples"]}
+        del A0, A
+
+    # accuracy against FP64 / FP32 (Sec. 5.1), n = 2048
+    if want("accuracy"):
+        acc = {}
+        A64 = torch.from_numpy(inputs.uniform((2048, 2048), 31)).to(dev)
+        acc["lu_2048"] = accuracy.solve_accuracy(A64, "lu")
+        S64 = torch.from_numpy(inputs.spd(2048, 32, device=dev)).to(dev)
+        acc["cholesky_2048"] = accuracy.solve_accuracy(S64, "cholesky")
+        out["accuracy"] = acc
+
+    # batched: 4096 problems, n log-uniform [16, 512], half LU half Cholesky
+    if want("batched"):
+        count = 4096
+        ns = inputs.batched_sizes(count, inputs.SEED_BASE + 3)
+        batched = {}
+        for chol, label in ((binding.POSIT_CHOLESKY, "cholesky_L"), (binding.POSIT_CHOLESKY_U, "cholesky_U")):
+            kinds = np.array([binding.POSIT_LU if i % 2 == 0 else chol for i in range(count)], np.int32)
+            ps = ProblemSet(kinds, ns, np.ones(count, np.int64))
+            for i in range(count):
+                k = int(ns[i])
+                a64 = torch.from_numpy(inputs.uniform((k, k), 7000 + i) if kinds[i] == 0
+                                       else inputs.spd(k, 7000 + i)).to(dev)
+                b64 = torch.from_numpy(inputs.uniform((k,), 9000 + i)).to(dev)
+                binding.posit_from_double(a64.T.contiguous(), ps.A[ps.a_off[i]:], k * k, stream)
+                binding.posit_from_double(b64, ps.B[ps.b_off[i]:], k, stream)
+            torch.cuda.synchronize()
+            snap = ps.snapshot()
+            best, timings = autotune.tune_problem_set(ps, sample=512, use_cache=True)
+            plan = plan_of(*best)
+            ws = torch.empty(ps.workspace_bytes(plan), dtype=torch.uint8, device=dev)
+            g = torch.cuda.CUDAGraph()
+            gs = torch.cuda.Stream()
+            ps.restore(snap)
+            with torch.cuda.graph(g, stream=gs):
+                ps.run(plan, ws, stream=gs)
+            ms = _time_ms(g.replay, torch.cuda.current_stream(), reps=2, setup=lambda: ps.restore(snap))
+            ops = float(sum((2 * k ** 3 / 3 if kd == 0 else k ** 3 / 3) + 2 * k * k
+                            for k, kd in zip(ns, kinds)))
+            sample = list(range(0, count, 16))
+            ps.restore(snap)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for i in sample:
+                k = int(ns[i])
+                Ai, Bi, Pi = ps.A[ps.a_off[i]:], ps.B[ps.b_off[i]:], ps.ipiv[ps.p_off[i]:]
+                if kinds[i] == 0:
+                    binding.posit_rgetrf(k, k, Ai, k, Pi, info, stream)
+                    binding.posit_rgetrs("N", k, 1, Ai, k, Pi, Bi, k, stream)
+                else:
+                    uplo = "U" if kinds[i] == binding.POSIT_CHOLESKY_U else "L"
+                    binding.posit_rpotrf(uplo, k, Ai, k, info, stream)
+                    binding.posit_rpotrs(uplo, k, 1, Ai, k, Bi, k, stream)
+            torch.cuda.synchronize()
+            plain_s = time.perf_counter() - t0
+            batched[label] = {"problems": count, "plan": list(best), "graph_ms": ms,
+                              "solves_per_s": count / (ms / 1e3), "gflops": ops / (ms / 1e3) / 1e9,
+                              "per_matrix_launches_solves_per_s": len(sample) / plain_s,
+                              "per_matrix_sample": f"every 16th problem ({len(sample)}), one stream"}
+            del ps, ws, g
+        out["batched"] = batched
+
+    # serving: Poisson 2000 req/s, n log-uniform [64, 4096], nrhs 1..8
+    if want("serving"):
+        serve = {}
+        for chol, label in ((binding.POSIT_CHOLESKY_U, "cholesky_U"), (binding.POSIT_CHOLESKY, "cholesky_L")):
+            pool = serving.Pool(96, 64, 4096, 8, seed=20240129, cholesky_kind=chol)
+            t, idx = serving.arrivals(2000.0, args.serve_seconds, pool.size, seed=7)
+            for name, small in (("continuous_batching", 512), ("per_request_plain", 1)):
+                cfg = serving.default_config(budget_gb=40.0, small_n_max=small)
+                r = serving.run(pool, t, idx, cfg, duration=args.serve_seconds, max_outstanding=256)
+                r.pop("kept")
+                serve[f"{label}/{name}"] = r
+            if chol == binding.POSIT_CHOLESKY_U:
+                # a rate the server sustains (offered work below its capacity)
+                rate = args.serve_rate_sustained
+                t2, idx2 = serving.arrivals(rate, args.serve_seconds, pool.size, seed=8)
+                for name, small in (("continuous_batching", 512), ("per_request_plain", 1)):
+                    cfg = serving.default_config(budget_gb=40.0, small_n_max=small)
+                    r = serving.run(pool, t2, idx2, cfg, duration=args.serve_seconds,
+                                    max_outstanding=256)
+                    r.pop("kept")
+                    serve[f"{label}/{name}@{rate:g}per_s"] = r
+            del pool
+        serve["workload"] = (f"Poisson 2000/s (and {args.serve_rate_sustained:g}/s), n log-uniform "
+                             f"[64, 4096], nrhs 1-8, LU/Cholesky 50/50, {args.serve_seconds:.0f} s, "
+                             "40 GB budget, pool of 96 seeded problems; latency from arrival "
+                             "(queueing included)")
+        out["serving"] = serve
+
+    return out
 
 
 def main():

@@ -31,8 +31,6 @@ namespace posit {
 namespace {
 
 constexpr int PT = 256;           // panel kernel threads
-constexpr int TRSM_NC = 32;       // trsm columns per CTA
-constexpr int TRSM_T = 256;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded barrier wait
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -341,52 +339,135 @@ __global__ void __launch_bounds__(PT, 1) panel_kernel(PanelArgs a) {
 }
 
 // The panel's row swaps (pivots k0 .. k1-1) applied to columns [c0, c1).
-__global__ void laswp_kernel(uint32_t *__restrict__ A, int64_t lda, int64_t c0, int64_t c1,
-                             int64_t k0, int64_t k1, const int32_t *__restrict__ ipiv) {
-  for (int64_t col = c0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; col < c1;
-       col += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t *cp = A + col * lda;
-    for (int64_t k = k0; k < k1; ++k) {
-      int64_t p = ipiv[k] - 1;
-      if (p != k) {
-        uint32_t t = cp[k];
-        cp[k] = cp[p];
-        cp[p] = t;
-      }
+// LAPACK row swaps k = k0 .. k1-1 (rows k and ipiv[k]-1, in that order) on
+// columns [c0, c1).  Each CTA first turns the sequence into one permutation
+// of at most 2 (k1 - k0) rows in shared memory: slot t < nk holds row k0 + t,
+// and each pivot row outside [k0, k1) gets the slot nk + (first swap that
+// names it); the swaps are then played on slot contents.  A warp then moves
+// one column at a time: it reads every displaced word, then writes them, so
+// a column costs two dependent memory round trips instead of one per swap.
+constexpr int LASWP_T = 256;
+constexpr int LASWP_MAXK = 256;  // swaps per launch (the panel width kNB)
+
+__global__ void __launch_bounds__(LASWP_T)
+laswp_kernel(uint32_t *__restrict__ A, int64_t lda, int64_t c0, int64_t c1, int64_t k0,
+             int64_t k1, const int32_t *__restrict__ ipiv) {
+  __shared__ int64_t piv[LASWP_MAXK];
+  __shared__ int64_t row_of[2 * LASWP_MAXK];   // slot -> matrix row
+  __shared__ int32_t slot_of[LASWP_MAXK];      // swap t -> slot of its pivot row
+  __shared__ int32_t content[2 * LASWP_MAXK];  // slot -> slot whose old word lands here
+  __shared__ int32_t moved[2 * LASWP_MAXK];    // the slots whose word changes
+  __shared__ int32_t nmoved;
+  __shared__ uint32_t buf[LASWP_T / 32][2 * LASWP_MAXK];
+  const int nk = (int)(k1 - k0);
+  const int tid = threadIdx.x;
+  for (int t = tid; t < nk; t += LASWP_T) piv[t] = (int64_t)ipiv[k0 + t] - 1;
+  __syncthreads();
+  for (int t = tid; t < nk; t += LASWP_T) {
+    const int64_t p = piv[t];
+    int slot;
+    if (p >= k0 && p < k1) {
+      slot = (int)(p - k0);
+    } else {
+      int first = t;
+      for (int u = 0; u < t; ++u)
+        if (piv[u] == p) { first = u; break; }
+      slot = nk + first;
     }
+    slot_of[t] = slot;
+    row_of[t] = k0 + t;
+    row_of[nk + t] = p;
+    content[t] = t;
+    content[nk + t] = nk + t;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int t = 0; t < nk; ++t) {
+      const int o = slot_of[t];
+      const int c = content[t];
+      content[t] = content[o];
+      content[o] = c;
+    }
+    int cnt = 0;
+    for (int sl = 0; sl < 2 * nk; ++sl)
+      if (content[sl] != sl) moved[cnt++] = sl;
+    nmoved = cnt;
+  }
+  __syncthreads();
+  const int lane = tid & 31, warp = tid >> 5;
+  const int nm = nmoved;
+  uint32_t *wb = buf[warp];
+  const int64_t nwarps = (int64_t)gridDim.x * (LASWP_T / 32);
+  for (int64_t col = c0 + (int64_t)blockIdx.x * (LASWP_T / 32) + warp; col < c1; col += nwarps) {
+    uint32_t *cp = A + col * lda;
+    for (int i = lane; i < nm; i += 32) wb[i] = cp[row_of[content[moved[i]]]];
+    __syncwarp();
+    for (int i = lane; i < nm; i += 32) cp[row_of[moved[i]]] = wb[i];
+    __syncwarp();
   }
 }
 
-// U12 <- L11^-1 A12 with L11 unit lower (jb x jb at (j, j)), A12 = rows
-// [j, j+jb) of columns [c0, c1).  Element (r, col) of U12 receives
+// U12 <- L11^-1 A12 with L11 unit lower (jb x jb at (j, j), jb <= 256), A12 =
+// rows [j, j+jb) of columns [c0, c1).  Element (r, col) of U12 receives
 // l_{r,t} * u_{t,col} for t = 0 .. r-1 in ascending order.
+//
+// One warp per column: lane l keeps rows l, l+32, ... of its column in
+// registers, u_t is broadcast by a shuffle from the lane that owns row t, so
+// the warps never wait for each other; a CTA of 8 warps shares 16 columns of
+// L11 at a time, decoded in shared memory.
+constexpr int TRSM_T = 256;
+constexpr int TRSM_CHUNK = 16;
+constexpr int TRSM_MAXJB = 256;
+
 __global__ void __launch_bounds__(TRSM_T)
 trsm_llu_kernel(uint32_t *__restrict__ A, int64_t lda, int64_t j, int jb, int64_t c0, int64_t c1) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  pz *X = reinterpret_cast<pz *>(smem_raw);   // [jb][TRSM_NC]
-  pz *Lc = X + (size_t)jb * TRSM_NC;          // [jb]
-  const int tid = threadIdx.x;
-  const int64_t cb = c0 + (int64_t)blockIdx.x * TRSM_NC;
-  const int nc = (int)min64(TRSM_NC, c1 - cb);
-  for (int idx = tid; idx < jb * TRSM_NC; idx += TRSM_T) {
-    int r = idx % jb, cc = idx / jb;
-    X[(size_t)r * TRSM_NC + cc] = cc < nc ? pz_decode(A[(j + r) + (cb + cc) * lda]) : pz_zero();
+  __shared__ pz Ls[TRSM_CHUNK][TRSM_MAXJB];  // Ls[u][r] = l_{r, t0+u}
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t col = c0 + (int64_t)blockIdx.x * (TRSM_T / 32) + warp;
+  const bool active = col < c1;  // warp-uniform
+  uint32_t *cp = A + j + col * lda;
+  pz xs[TRSM_MAXJB / 32];
+#pragma unroll
+  for (int i = 0; i < TRSM_MAXJB / 32; ++i) {
+    const int r = 32 * i + lane;
+    xs[i] = (active && r < jb) ? pz_decode(cp[r]) : pz_zero();
   }
-  for (int t = 0; t + 1 < jb; ++t) {
-    for (int r = t + 1 + tid; r < jb; r += TRSM_T) Lc[r] = pz_decode(A[(j + r) + (j + t) * lda]);
-    __syncthreads();
-    const int nr = jb - t - 1;
-    for (int idx = tid; idx < nr * TRSM_NC; idx += TRSM_T) {
-      int r = t + 1 + idx / TRSM_NC, cc = idx % TRSM_NC;
-      if (cc >= nc) continue;
-      pz *x = &X[(size_t)r * TRSM_NC + cc];
-      *x = pz_sub(*x, pz_mul(Lc[r], X[(size_t)t * TRSM_NC + cc]));
+#pragma unroll
+  for (int i0 = 0; i0 < TRSM_MAXJB / 32; ++i0) {
+    if (32 * i0 >= jb - 1) break;  // rows from 32*i0 on have nothing below them to update
+#pragma unroll 1
+    for (int h = 0; h < 32 / TRSM_CHUNK; ++h) {
+      const int t0 = 32 * i0 + TRSM_CHUNK * h;
+      if (t0 >= jb - 1) break;
+      __syncthreads();
+      for (int idx = tid; idx < TRSM_CHUNK * jb; idx += TRSM_T) {
+        const int u = idx / jb, r = idx - u * jb;
+        const int t = t0 + u;
+        Ls[u][r] = (r > t && t < jb) ? pz_decode(A[(j + r) + (j + t) * lda]) : pz_zero();
+      }
+      __syncthreads();
+      if (active) {
+        const int un = min(TRSM_CHUNK, jb - 1 - t0);
+        for (int u = 0; u < un; ++u) {
+          const int t = t0 + u;
+          const int owner = t & 31;
+          const pz xt{__shfl_sync(0xFFFFFFFFu, xs[i0].s, owner),
+                      __shfl_sync(0xFFFFFFFFu, xs[i0].m, owner)};
+#pragma unroll
+          for (int i = i0; i < TRSM_MAXJB / 32; ++i) {
+            const int r = 32 * i + lane;
+            if (r > t && r < jb) xs[i] = pz_sub(xs[i], pz_mul(Ls[u][r], xt));
+          }
+        }
+      }
     }
-    __syncthreads();
   }
-  for (int idx = tid; idx < jb * TRSM_NC; idx += TRSM_T) {
-    int r = idx % jb, cc = idx / jb;
-    if (cc < nc) A[(j + r) + (cb + cc) * lda] = pz_to_bits(X[(size_t)r * TRSM_NC + cc]);
+  if (active) {
+#pragma unroll
+    for (int i = 0; i < TRSM_MAXJB / 32; ++i) {
+      const int r = 32 * i + lane;
+      if (r < jb) cp[r] = pz_to_bits(xs[i]);
+    }
   }
 }
 
@@ -488,20 +569,18 @@ int launch_panel(PanelArgs &pa, const PanelShape &ps, cudaStream_t stream) {
 int trsm_llu(uint32_t *A, int64_t lda, int64_t j, int jb, int64_t c0, int64_t c1,
              cudaStream_t stream) {
   if (c1 <= c0 || jb <= 1) return POSIT_OK;
-  size_t smem = ((size_t)jb * TRSM_NC + jb) * sizeof(pz);
-  if (cudaFuncSetAttribute(trsm_llu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem) != cudaSuccess)
-    return POSIT_ERR_CUDA;
-  dim3 grid((unsigned)ceil_div(c1 - c0, TRSM_NC));
-  trsm_llu_kernel<<<grid, TRSM_T, smem, stream>>>(A, lda, j, jb, c0, c1);
+  if (jb > TRSM_MAXJB) return POSIT_ERR_DEVICE;  // never: panels are at most kNB wide
+  dim3 grid((unsigned)ceil_div(c1 - c0, TRSM_T / 32));
+  trsm_llu_kernel<<<grid, TRSM_T, 0, stream>>>(A, lda, j, jb, c0, c1);
   return launch_status();
 }
 
 int laswp(uint32_t *A, int64_t lda, int64_t c0, int64_t c1, int64_t k0, int64_t k1,
           const int32_t *ipiv, cudaStream_t stream) {
   if (c1 <= c0 || k1 <= k0) return POSIT_OK;
-  int64_t blocks = min64(ceil_div(c1 - c0, 128), 152 * 8);
-  laswp_kernel<<<(unsigned)blocks, 128, 0, stream>>>(A, lda, c0, c1, k0, k1, ipiv);
+  if (k1 - k0 > LASWP_MAXK) return POSIT_ERR_DEVICE;  // never: swaps come per panel
+  int64_t blocks = min64(ceil_div(c1 - c0, LASWP_T / 32), 152 * 4);
+  laswp_kernel<<<(unsigned)blocks, LASWP_T, 0, stream>>>(A, lda, c0, c1, k0, k1, ipiv);
   return launch_status();
 }
 

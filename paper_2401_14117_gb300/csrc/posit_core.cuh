@@ -93,11 +93,18 @@ static __device__ __noinline__ uint32_t pz_encode(uint32_t sign, int S, uint32_t
   return sign ? (0u - p) : p;
 }
 
-// Word of an already rounded decoded value (exact, no rounding happens).
+// Word of an already rounded decoded value (exact, no rounding happens).  The
+// pattern after the sign is the regime (k+1 ones and a zero, or -k zeros and a
+// one) followed by the 2 exponent bits and 27 fraction bits, cut to 31 bits;
+// the bits cut off are zero because the value is a posit.
 static __device__ __forceinline__ uint32_t pz_to_bits(pz a) {
   if (pz_is_nar(a)) return PZ_NAR_BITS;
   if (pz_is_zero(a)) return 0u;
-  return pz_encode(a.m & 0x80000000u, a.s, a.m & 0x7FFFFFFFu);
+  const int k = a.s >> 2;  // -30 .. 30 for every rounded value
+  const uint32_t body = ((uint32_t)(a.s & 3) << 27) | ((a.m & 0x3FFFFFFFu) >> 3);
+  const uint32_t pay = k >= 0 ? ((0x7FFFFFFFu ^ (0x7FFFFFFFu >> (k + 1))) | (body >> k))
+                              : ((1u << (30 + k)) | (body >> (-1 - k)));
+  return (a.m >> 31) ? (0u - pay) : pay;
 }
 
 // Slow rounding for regimes of 28 or more bits (S <= -109 or S >= 108).

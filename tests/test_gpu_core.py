@@ -86,6 +86,23 @@ def test_elementwise_matches_oracle(op, code):
     assert bad.size == 0, [(hex(a[i]), hex(b[i]), hex(got[i]), hex(want[i])) for i in bad[:5]]
 
 
+@pytest.mark.parametrize("offset,count", [(1, 1001), (2, 4099), (0, 4097), (3, 3)])
+def test_elementwise_unaligned_and_ragged(offset, count):
+    """Operands that start off a 16-byte boundary (one word at a time) and
+    counts that are not a multiple of 4 (the vector tail)."""
+    rng = np.random.default_rng(20 + offset)
+    a = mixed_words(rng, count + 16)
+    b = mixed_words(rng, count + 16)
+    da, db = words_to_dev(a), words_to_dev(b)
+    for op, code in (("add", 0), ("mul", 2), ("div", 3), ("sqrt", 4)):
+        want = oracle.elementwise(op, a[offset:offset + count], b[offset:offset + count])
+        dr = torch.zeros(count + 16, dtype=torch.int32, device=DEV)
+        binding.posit_elementwise(code, da[offset:], db[offset:], dr[offset:], count)
+        got = words_from_dev(dr)
+        assert np.array_equal(got[offset:offset + count], want), op
+        assert not got[:offset].any() and not got[offset + count:].any(), op
+
+
 @pytest.mark.parametrize("op", ["sqrt", "recip"])
 def test_unary_strided_over_all_words(op):
     """sqrt and reciprocal (1 / x) on every 61st word of the 2^32."""
