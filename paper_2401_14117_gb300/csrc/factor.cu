@@ -39,29 +39,38 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // Grid barrier over `nblocks` co-resident CTAs (cooperative launch).  bar[0]
-// counts arrivals, bar[1] is the generation.  Returns false after a timeout.
+// is a counter of arrivals that only grows (the host zeroes it before each
+// launch): the CTA whose arrival returns `old` waits until the counter
+// reaches the next multiple of nblocks.  One atomic per CTA and a spin on an
+// acquire load; the error flag and the clock are looked at every 256 polls,
+// and the wait gives up after about 2 s of global time.  Returns false after
+// a timeout (or another CTA's).
 __device__ bool grid_barrier(unsigned *bar, unsigned nblocks, int *err, int32_t *info) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned *vgen = bar + 1;
-    unsigned gen = *vgen;
     __threadfence();
-    unsigned arrived = atomicAdd(bar, 1u);
-    if (arrived == nblocks - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      unsigned long long t0 = global_ns();
-      while (*vgen == gen) {
+    const unsigned old = atomicAdd(bar, 1u);
+    const unsigned target = (old / nblocks + 1u) * nblocks;
+    unsigned long long t0 = 0;
+    unsigned polls = 0;
+    while ((int)(ld_acquire(bar) - target) < 0) {
+      if ((++polls & 255u) == 0u) {
         if (*(volatile int *)err) break;
-        if (global_ns() - t0 > kWaitNs) {
+        const unsigned long long now = global_ns();
+        if (t0 == 0) {
+          t0 = now;
+        } else if (now - t0 > kWaitNs) {
           atomicExch(err, 1);
           atomicExch(info, POSIT_ERR_TIMEOUT);
           break;
         }
-        __nanosleep(100);
       }
     }
     __threadfence();
@@ -558,6 +567,8 @@ int launch_panel(PanelArgs &pa, const PanelShape &ps, cudaStream_t stream) {
   if (cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)ps.smem) != cudaSuccess)
     return POSIT_ERR_CUDA;
+  // the grid barrier's arrival counter starts at zero in every launch
+  if (cudaMemsetAsync(pa.bar, 0, sizeof(unsigned), stream) != cudaSuccess) return POSIT_ERR_CUDA;
   pa.jb = ps.jb;
   pa.R = ps.R;
   void *args[] = {&pa};

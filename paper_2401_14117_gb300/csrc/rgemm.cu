@@ -35,6 +35,7 @@ constexpr int BM = 128, BN = 64, BK = 16;
 constexpr int TM = 4, TN = 4;
 constexpr int NT = 512;  // (BM / TM) * (BN / TN)
 constexpr int GM = BM / TM;
+constexpr int64_t kGroupM = 16;  // row tiles per group of the launch order
 static_assert((BM / TM) * (BN / TN) == NT, "thread tile");
 
 template <int TRI>
@@ -57,7 +58,16 @@ rgemm_kernel(int64_t M, int64_t N, int64_t K, uint32_t alpha,
   const int tid = threadIdx.x;
   const int tm = tid % GM;  // row group: rows tm*TM .. +TM-1
   const int tn = tid / GM;  // column group (one warp): cols tn*TN .. +TN-1
-  const int64_t m0 = (int64_t)blockIdx.x * BM;
+  // Grouped launch order (full matrices with more than kGroupM row tiles):
+  // the grid is (kGroupM row tiles, column tiles, groups; the last group may
+  // be partial), so consecutive CTAs take kGroupM row tiles by a run of
+  // column tiles, and a wave of CTAs streams the k slices of about 2048 rows
+  // of op(A) and 1200 columns of op(B), which the CTAs that share them then
+  // read from L2 instead of each from DRAM.  Otherwise the grid is (row
+  // tiles, column tiles, 1).
+  const unsigned mt = blockIdx.z * (unsigned)kGroupM + blockIdx.x;
+  if (mt >= (unsigned)((M + BM - 1) / BM)) return;  // the last group may be partial
+  const int64_t m0 = (int64_t)mt * BM;
   const int64_t n0 = (int64_t)blockIdx.y * BN;
   if (TRI == TRI_LOWER && n0 > m0 + BM - 1) return;  // tile wholly above diagonal
   if (TRI == TRI_UPPER && m0 > n0 + BN - 1) return;  // tile wholly below diagonal
@@ -171,30 +181,50 @@ rgemm_kernel(int64_t M, int64_t N, int64_t K, uint32_t alpha,
   }
 }
 
+template <bool TA, bool TB, int TRI>
+int launch_one(dim3 grid, int64_t m, int64_t n, int64_t k, uint32_t alpha, const uint32_t *A,
+               int64_t lda, const uint32_t *B, int64_t ldb, uint32_t beta, uint32_t *C,
+               int64_t ldc, const int32_t *abort_flag, cudaStream_t stream) {
+  rgemm_kernel<TA, TB, TRI><<<grid, NT, 0, stream>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
+                                                      abort_flag);
+  return launch_status();
+}
+
+template <int TRI>
+int launch_shape(bool ta, bool tb, dim3 grid, int64_t m, int64_t n, int64_t k, uint32_t alpha,
+                 const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb, uint32_t beta,
+                 uint32_t *C, int64_t ldc, const int32_t *abort_flag, cudaStream_t stream) {
+  if (!ta && !tb)
+    return launch_one<false, false, TRI>(grid, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, abort_flag, stream);
+  if (!ta && tb)
+    return launch_one<false, true, TRI>(grid, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, abort_flag, stream);
+  if (ta && !tb)
+    return launch_one<true, false, TRI>(grid, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, abort_flag, stream);
+  return launch_one<true, true, TRI>(grid, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, abort_flag, stream);
+}
+
 template <int TRI>
 int launch_tri(bool ta, bool tb, int64_t m, int64_t n, int64_t k, uint32_t alpha,
                const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb,
                uint32_t beta, uint32_t *C, int64_t ldc, const int32_t *abort_flag,
                cudaStream_t stream) {
   const int64_t gx = ceil_div(m, BM);
+  if (gx > 0x7FFFFFFF) return POSIT_ERR_DEVICE;
   // gridDim.y is limited to 65535: split very wide C into column chunks
   const int64_t max_cols = (int64_t)65535 * BN;
   for (int64_t c0 = 0; c0 < n; c0 += max_cols) {
-    int64_t nc = min64(max_cols, n - c0);
-    dim3 grid((unsigned)gx, (unsigned)ceil_div(nc, BN));
+    const int64_t nc = min64(max_cols, n - c0);
+    const unsigned gy = (unsigned)ceil_div(nc, BN);
     const uint32_t *Bp = tb ? B + c0 : B + c0 * ldb;
     uint32_t *Cp = C + c0 * ldc;
     // a column chunk of a triangular update keeps its global diagonal: the
     // chunked path is only used for TRI_FULL (n <= 4M columns otherwise)
-    if (!ta && !tb)
-      rgemm_kernel<false, false, TRI><<<grid, NT, 0, stream>>>(m, nc, k, alpha, A, lda, Bp, ldb, beta, Cp, ldc, abort_flag);
-    else if (!ta && tb)
-      rgemm_kernel<false, true, TRI><<<grid, NT, 0, stream>>>(m, nc, k, alpha, A, lda, Bp, ldb, beta, Cp, ldc, abort_flag);
-    else if (ta && !tb)
-      rgemm_kernel<true, false, TRI><<<grid, NT, 0, stream>>>(m, nc, k, alpha, A, lda, Bp, ldb, beta, Cp, ldc, abort_flag);
-    else
-      rgemm_kernel<true, true, TRI><<<grid, NT, 0, stream>>>(m, nc, k, alpha, A, lda, Bp, ldb, beta, Cp, ldc, abort_flag);
-    int st = launch_status();
+    const int64_t groups = ceil_div(gx, kGroupM);
+    const dim3 grid = (TRI == TRI_FULL && gx > kGroupM && groups <= 65535)
+                          ? dim3((unsigned)kGroupM, gy, (unsigned)groups)
+                          : dim3((unsigned)gx, gy, 1);
+    int st = launch_shape<TRI>(ta, tb, grid, m, nc, k, alpha, A, lda, Bp, ldb, beta, Cp, ldc,
+                               abort_flag, stream);
     if (st != POSIT_OK) return st;
   }
   return POSIT_OK;

@@ -57,6 +57,19 @@ def test_shapes_and_tails(m, n, k):
     assert_same(run_gpu("N", "N", ONE, A, B, ONE, C), oracle.rgemm("N", "N", ONE, A, B, ONE, C))
 
 
+@pytest.mark.parametrize("ta,tb", list(itertools.product("NT", "NT")))
+@pytest.mark.parametrize("m", [2048, 2500, 4223])
+def test_grouped_launch_order_and_remainder(ta, tb, m):
+    """More than 16 row tiles: complete groups of 16 row tiles in the grouped
+    launch order, plus (for 2500 and 4223) the remaining row tiles launched
+    as a matrix of their own."""
+    n, k = 70, 23
+    A = words((m, k) if ta == "N" else (k, m), m + 1)
+    B = words((k, n) if tb == "N" else (n, k), m + 2)
+    C = words((m, n), m + 3)
+    assert_same(run_gpu(ta, tb, MONE, A, B, ONE, C), oracle.rgemm(ta, tb, MONE, A, B, ONE, C))
+
+
 def test_special_values_inside_matrices():
     """Zeros, NaR, huge and tiny entries: the zero/NaR sentinels and the
     exponent-truncated rounding band inside the GEMM."""
