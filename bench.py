@@ -14,7 +14,8 @@ The line also carries:
   roofline      integer-issue roofline of the rgemm kernel: warp instructions
                 issued per second (instructions per launch from ncu's
                 smsp__inst_executed.sum, scaled per multiply-add) against
-                SMs x 4 schedulers x max SM clock
+                SMs x 4 schedulers x max SM clock; traffic = DRAM bytes of
+                one 8192^3 launch from the same ncu capture
   e2e           the same metric measured with host buffers: host->device copy
                 of A and B, the call, device->host copy of C, every step
   cpu_baseline  the CPU oracle (plain C, OpenMP) on a bounded sample of the
@@ -38,10 +39,14 @@ UNIT = "Gflops"
 ONE = 0x40000000
 
 # Warp instructions the rgemm kernel issues per posit multiply-add:
-# smsp__inst_executed.sum / (M N K) of one ncu capture of the current kernel
-# (NN, 2048^3, uniform [-1,1]: 2.3357e10 / 8.590e9; profiles/rgemm_nn_ncu.md).
-# The count is set by the inner loop, so it scales with M N K.
-INST_PER_MAC = 2.7191
+# smsp__inst_executed.sum / (M N K) of one ncu capture of one launch of the
+# current kernel on the default workload (NN 8192^3, uniform [-1,1]:
+# 1.49425e12 / 5.4976e11; at 2048^3 the same kernel gives 2.7188).  The
+# count is set by the inner loop, so it scales with M N K.
+INST_PER_MAC = 2.7180
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of that same
+# captured 8192^3 launch: 4.96 GB read + 0.42 GB written.
+TRAFFIC_8192 = 4.96e9 + 0.41894e9
 SM_COUNT = 152
 SCHEDULERS_PER_SM = 4
 
@@ -336,8 +341,11 @@ def run_ours(args):
         frac = achieved / peak
     else:
         achieved = frac = None
+    traffic = TRAFFIC_8192 if (m, n, k) == (8192, 8192, 8192) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gwarp-inst/s",
-                "frac": frac, "traffic": None, "kernel": "rgemm_kernel<false,false,0>",
+                "frac": frac, "traffic": traffic, "traffic_unit": "bytes per launch",
+                "algorithmic_bytes": 4.0 * (m * k + k * n + m * n),
+                "kernel": "rgemm_kernel<false,false,0>",
                 "launch_ms": launch_ms, "inst_per_mac": INST_PER_MAC,
                 "peak_basis": f"{SM_COUNT} SMs x {SCHEDULERS_PER_SM} schedulers x 1 warp-inst/clk x {peak_clock:.0f} MHz"}
 
@@ -596,6 +604,7 @@ def extras(args, dev, stream):
     if want("batched"):
         count = 4096
         ns = inputs.batched_sizes(count, inputs.SEED_BASE + 3)
+        info = torch.zeros(1, dtype=torch.int32, device=dev)
         batched = {}
         for chol, label in ((binding.POSIT_CHOLESKY, "cholesky_L"), (binding.POSIT_CHOLESKY_U, "cholesky_U")):
             kinds = np.array([binding.POSIT_LU if i % 2 == 0 else chol for i in range(count)], np.int32)

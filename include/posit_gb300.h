@@ -189,9 +189,10 @@ POSIT_API int posit_rpotrs(char uplo, int64_t n, int64_t nrhs, const posit32_t *
  * plan: launch shape (any valid plan gives the same results):
  *   threads      threads per CTA (multiple of 32, <= 1024)
  *   ctas_per_sm  persistent CTAs per SM
- *   smem_bytes   shared memory per CTA; a problem whose n*n + 2*n*nrhs
- *                decoded elements (8 bytes each) fit is kept there,
- *                others use the CTA's slice of the workspace.
+ *   smem_bytes   shared memory per CTA; a problem whose
+ *                n*n + n*nrhs + n*max(nrhs, 1) decoded elements (8 bytes
+ *                each) fit is kept there, others use the CTA's slice of
+ *                the workspace.
  * workspace: DEVICE memory of posit_batched_workspace_size() bytes, or NULL
  * to allocate it stream-ordered inside the call.  With a workspace the call
  * performs no allocation and enqueues one memset and one kernel.

@@ -52,9 +52,32 @@ __device__ Key block_argmax(uint64_t k, int r, Key *red) {
   return out;
 }
 
+// One rounded multiply and one rounded subtract, x - a*b.  FAST uses the
+// per-scale rounding table and is exact for operands that are not NaR (a
+// problem whose matrix holds no NaR never creates one while it is factored:
+// zero pivots are skipped and Cholesky stops at the first d <= 0); otherwise
+// the general operations propagate NaR.
+template <bool FAST>
+__device__ __forceinline__ pz sub_mul(const pz_rtab *tab, pz x, pz a, pz b) {
+  if (FAST) {
+    const pz p = pz_mul_tab(tab, a, b);
+    return pz_add_tab(tab, x, pz{p.s, p.m ^ 0x80000000u});
+  }
+  return pz_sub(x, pz_mul(a, b));
+}
+
+template <bool FAST>
+__device__ __forceinline__ pz mul_any(const pz_rtab *tab, pz a, pz b) {
+  return FAST ? pz_mul_tab(tab, a, b) : pz_mul(a, b);
+}
+
 // LU with partial pivoting of the decoded n x n matrix M (column-major, ld n).
-__device__ int lu_decoded(pz *M, int n, int32_t *ipiv, Key *red, pz *sh) {
+// The rank-1 update runs with the lanes of a warp on consecutive rows and the
+// warps on columns.
+template <bool FAST>
+__device__ int lu_decoded(pz *M, int n, int32_t *ipiv, Key *red, pz *sh, const pz_rtab *tab) {
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   int info = 0;
   for (int c = 0; c < n; ++c) {
     uint64_t best = 0;
@@ -81,14 +104,15 @@ __device__ int lu_decoded(pz *M, int n, int32_t *ipiv, Key *red, pz *sh) {
       if (tid == 0) sh[0] = pz_div(pz_one(), M[c + (size_t)c * n]);
       __syncthreads();
       const pz r = sh[0];
-      for (int i = c + 1 + tid; i < n; i += nt) M[i + (size_t)c * n] = pz_mul(M[i + (size_t)c * n], r);
+      for (int i = c + 1 + tid; i < n; i += nt)
+        M[i + (size_t)c * n] = mul_any<FAST>(tab, M[i + (size_t)c * n], r);
     }
     __syncthreads();
-    const int m = n - c - 1;
-    for (int idx = tid; idx < m * m; idx += nt) {
-      int i = c + 1 + idx % m, k = c + 1 + idx / m;
-      pz *x = &M[i + (size_t)k * n];
-      *x = pz_sub(*x, pz_mul(M[i + (size_t)c * n], M[c + (size_t)k * n]));
+    const pz *lc = M + (size_t)c * n;
+    for (int k = c + 1 + warp; k < n; k += nw) {
+      pz *col = M + (size_t)k * n;
+      const pz u = col[c];
+      for (int i = c + 1 + lane; i < n; i += 32) col[i] = sub_mul<FAST>(tab, col[i], lc[i], u);
     }
     __syncthreads();
   }
@@ -96,8 +120,10 @@ __device__ int lu_decoded(pz *M, int n, int32_t *ipiv, Key *red, pz *sh) {
 }
 
 // Cholesky (lower) of the decoded matrix; returns info.
-__device__ int chol_decoded(pz *M, int n, pz *sh) {
+template <bool FAST>
+__device__ int chol_decoded(pz *M, int n, pz *sh, const pz_rtab *tab) {
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   for (int j = 0; j < n; ++j) {
     pz d = M[j + (size_t)j * n];
     if (pz_is_nar(d) || pz_is_zero(d) || (d.m >> 31)) return j + 1;
@@ -109,14 +135,15 @@ __device__ int chol_decoded(pz *M, int n, pz *sh) {
     __syncthreads();
     if (tid == 0) M[j + (size_t)j * n] = sh[0];
     const pz r = sh[1];
-    for (int i = j + 1 + tid; i < n; i += nt) M[i + (size_t)j * n] = pz_mul(M[i + (size_t)j * n], r);
+    for (int i = j + 1 + tid; i < n; i += nt)
+      M[i + (size_t)j * n] = mul_any<FAST>(tab, M[i + (size_t)j * n], r);
     __syncthreads();
-    const int m = n - j - 1;
-    for (int idx = tid; idx < m * m; idx += nt) {
-      int i = j + 1 + idx % m, k = j + 1 + idx / m;
-      if (k > i) continue;
-      pz *x = &M[i + (size_t)k * n];
-      *x = pz_sub(*x, pz_mul(M[i + (size_t)j * n], M[k + (size_t)j * n]));
+    // a_ik -= l_ij l_kj for j < k <= i: column k from row k down
+    const pz *lj = M + (size_t)j * n;
+    for (int k = j + 1 + warp; k < n; k += nw) {
+      pz *col = M + (size_t)k * n;
+      const pz u = lj[k];
+      for (int i = k + lane; i < n; i += 32) col[i] = sub_mul<FAST>(tab, col[i], lj[i], u);
     }
     __syncthreads();
   }
@@ -126,8 +153,10 @@ __device__ int chol_decoded(pz *M, int n, pz *sh) {
 // Cholesky (upper, A = U^T U) of the decoded matrix; returns info.  The
 // transposed mirror of chol_decoded: row j is scaled, the trailing upper
 // triangle updated.
-__device__ int chol_decoded_upper(pz *M, int n, pz *sh) {
+template <bool FAST>
+__device__ int chol_decoded_upper(pz *M, int n, pz *sh, const pz_rtab *tab, pz *row) {
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   for (int j = 0; j < n; ++j) {
     pz d = M[j + (size_t)j * n];
     if (pz_is_nar(d) || pz_is_zero(d) || (d.m >> 31)) return j + 1;
@@ -139,14 +168,17 @@ __device__ int chol_decoded_upper(pz *M, int n, pz *sh) {
     __syncthreads();
     if (tid == 0) M[j + (size_t)j * n] = sh[0];
     const pz r = sh[1];
-    for (int k = j + 1 + tid; k < n; k += nt) M[j + (size_t)k * n] = pz_mul(M[j + (size_t)k * n], r);
+    for (int k = j + 1 + tid; k < n; k += nt) {
+      const pz v = mul_any<FAST>(tab, M[j + (size_t)k * n], r);
+      M[j + (size_t)k * n] = v;
+      row[k] = v;  // row j of U, contiguous
+    }
     __syncthreads();
-    const int m = n - j - 1;
-    for (int idx = tid; idx < m * m; idx += nt) {
-      int i = j + 1 + idx % m, k = j + 1 + idx / m;
-      if (i > k) continue;
-      pz *x = &M[i + (size_t)k * n];
-      *x = pz_sub(*x, pz_mul(M[j + (size_t)i * n], M[j + (size_t)k * n]));
+    // a_ik -= u_ji u_jk for j < i <= k: column k from row j+1 to row k
+    for (int k = j + 1 + warp; k < n; k += nw) {
+      pz *col = M + (size_t)k * n;
+      const pz u = row[k];
+      for (int i = j + 1 + lane; i <= k; i += 32) col[i] = sub_mul<FAST>(tab, col[i], row[i], u);
     }
     __syncthreads();
   }
@@ -257,7 +289,10 @@ __global__ void batched_kernel(const posit_problem *__restrict__ probs,
   __shared__ Key red[33];
   __shared__ pz sh[2];
   __shared__ long long s_idx;
+  __shared__ int s_nar;
+  __shared__ pz_rtab rtab[256];
   const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < 256; i += nt) rtab[i] = pz_rtab_entry(i);
   pz *ws = workspace + (size_t)blockIdx.x * ws_elems_per_cta;
   for (;;) {
     if (tid == 0) {
@@ -270,30 +305,41 @@ __global__ void batched_kernel(const posit_problem *__restrict__ probs,
     if (qi < 0) break;
     const posit_problem P = probs[order ? order[qi] : qi];
     const int n = P.n, nrhs = P.nrhs;
-    const size_t need = (size_t)n * n + (size_t)n * nrhs + (size_t)n * nrhs;
+    // M (n x n), X (n x nrhs), then scratch of n * max(nrhs, 1): the products
+    // of the dot-form solve, or row j of U in the upper Cholesky
+    const size_t need = (size_t)n * n + (size_t)n * nrhs + (size_t)n * (nrhs > 1 ? nrhs : 1);
     pz *M = need <= (size_t)smem_elems ? sm : ws;
     pz *X = M + (size_t)n * n;
     pz *prod = X + (size_t)n * nrhs;
     const bool lower_only = P.kind == POSIT_CHOLESKY, upper_only = P.kind == POSIT_CHOLESKY_U;
+    if (tid == 0) s_nar = 0;
+    __syncthreads();
+    int nar = 0;
     for (int idx = tid; idx < n * n; idx += nt) {
       int i = idx % n, k = idx / n;
       bool skip = (lower_only && k > i) || (upper_only && k < i);
-      M[idx] = skip ? pz_zero() : pz_decode(P.A[i + (int64_t)k * P.lda]);
+      const uint32_t w = skip ? 0u : P.A[i + (int64_t)k * P.lda];
+      nar |= w == PZ_NAR_BITS;
+      M[idx] = pz_decode(w);
     }
+    if (__syncthreads_or(nar) && tid == 0) s_nar = 1;
     for (int idx = tid; idx < n * nrhs; idx += nt) {
       int i = idx % n, c = idx / n;
       X[idx] = pz_decode(P.B[i + (int64_t)c * P.ldb]);
     }
     __syncthreads();
+    const bool fast = s_nar == 0;  // the matrix holds no NaR
     int info;
     if (P.kind == POSIT_LU) {
-      info = lu_decoded(M, n, P.ipiv, red, sh);
+      info = fast ? lu_decoded<true>(M, n, P.ipiv, red, sh, rtab)
+                  : lu_decoded<false>(M, n, P.ipiv, red, sh, rtab);
       getrs_decoded(M, n, P.ipiv, X, nrhs);
     } else if (P.kind == POSIT_CHOLESKY) {
-      info = chol_decoded(M, n, sh);
+      info = fast ? chol_decoded<true>(M, n, sh, rtab) : chol_decoded<false>(M, n, sh, rtab);
       if (info == 0) potrs_decoded(M, n, X, nrhs, prod);
     } else {
-      info = chol_decoded_upper(M, n, sh);
+      info = fast ? chol_decoded_upper<true>(M, n, sh, rtab, prod)
+                  : chol_decoded_upper<false>(M, n, sh, rtab, prod);
       if (info == 0) potrs_decoded_upper(M, n, X, nrhs);
     }
     __syncthreads();
@@ -315,7 +361,8 @@ __global__ void batched_kernel(const posit_problem *__restrict__ probs,
 }  // namespace
 
 size_t batched_ws_elems(int max_n, int max_nrhs) {
-  return (size_t)max_n * max_n + 2 * (size_t)max_n * max_nrhs;
+  return (size_t)max_n * max_n + (size_t)max_n * max_nrhs +
+         (size_t)max_n * (max_nrhs > 1 ? max_nrhs : 1);
 }
 
 int batched_launch(const posit_problem *probs, const int32_t *order, int64_t count, int max_n,

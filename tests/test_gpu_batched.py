@@ -29,6 +29,12 @@ def make_set(kinds, ns, nrhs, seed):
 
 
 def expected(kind, A, B):
+    if B.shape[1] == 0:  # no right-hand side: the factorisation only
+        if kind == L:
+            F, ipiv, info = oracle.rgetrf(A)
+            return F, B, ipiv, info
+        F, info = oracle.rpotrf(A, uplo="U" if kind == CU else "L")
+        return F, B, None, info
     if kind == L:
         F, ipiv, info = oracle.rgetrf(A)
         X = oracle.rgetrs(F, ipiv, B)
@@ -96,6 +102,29 @@ def test_batched_singular_and_not_positive_definite():
     F, X, ip, info = ps.get_problem(1)
     assert info == 21 and np.array_equal(X, B1)
     check(ps, host, [0, 2, 3])
+
+
+def test_batched_nar_and_no_right_hand_side():
+    """NaR inside a matrix takes the general arithmetic (NaR propagates
+    exactly as in the single-problem routines); nrhs = 0 factors only."""
+    kinds = np.array([L, C, CU, L, C, CU, L, C], np.int32)
+    ns = np.array([20, 20, 20, 33, 40, 17, 150, 150])
+    nrhs = np.array([1, 2, 1, 0, 0, 0, 0, 3])
+    ps, host = make_set(kinds, ns, nrhs, 11)
+    NAR = np.uint32(0x80000000)
+    for i in (0, 1, 2, 7):
+        A, B = host[i]
+        A = A.copy()
+        A[3, 5] = NAR
+        A[5, 3] = NAR
+        ps.set_problem(i, A, B)
+        host[i] = (A, B)
+    for plan in (PLANS[0], PLANS[2]):
+        snap = ps.snapshot()
+        ps.run(plan_of(*plan))
+        torch.cuda.synchronize()
+        check(ps, host)
+        ps.restore(snap)
 
 
 def test_batched_workload_sampled():
