@@ -153,6 +153,30 @@ static __device__ __forceinline__ pz_rtab pz_rtab_entry(int i) {
   return e;
 }
 
+// Table for operands known to stay inside the fast band (see pz_round_inband):
+// the same constants, except that every scale outside it gets q = 30, which
+// leaves a zero significand zero (the only thing that can index those rows
+// then is the zero scale, clamped to row 255).
+static __device__ __forceinline__ pz_rtab pz_rtab_inband_entry(int i) {
+  pz_rtab e = pz_rtab_entry(i);
+  if (e.q > 31u) {
+    e.keep = 0xC0000000u; e.hm1 = (1u << 29) - 1u; e.q = 30u;
+  }
+  return e;
+}
+
+// pz_round_tab without the test for the regimes of 28 or more bits: only for
+// values whose scale is in [-108, 107] or that are zero (significand 0), with
+// the table of pz_rtab_inband_entry.
+static __device__ __forceinline__ pz pz_round_inband(const pz_rtab *tab, uint32_t sign, int S,
+                                                     uint32_t X) {
+  const pz_rtab e = tab[min((unsigned)(S + 128), 255u)];
+  uint32_t lsb = (X >> e.q) & 1u;
+  uint32_t r = (X + e.hm1 + lsb) & e.keep;
+  uint32_t c = r >> 31;
+  return pz{S + (int)c, sign | (r >> c)};
+}
+
 // pz_round with the per-scale constants read from the table.
 static __device__ __forceinline__ pz pz_round_tab(const pz_rtab *tab, uint32_t sign, int S,
                                                   uint32_t X) {
@@ -197,6 +221,13 @@ static __device__ __forceinline__ pz pz_mul_fast(pz a, pz b) {
   int S;
   pz_mul_exact(a, b, sign, S, X);
   return pz_round(sign, S, X);
+}
+
+static __device__ __forceinline__ pz pz_mul_inband(const pz_rtab *tab, pz a, pz b) {
+  uint32_t sign, X;
+  int S;
+  pz_mul_exact(a, b, sign, S, X);
+  return pz_round_inband(tab, sign, S, X);
 }
 
 static __device__ __forceinline__ pz pz_mul_tab(const pz_rtab *tab, pz a, pz b) {
@@ -245,6 +276,13 @@ static __device__ __forceinline__ pz pz_add_fast(pz c, pz t) {
   int S;
   pz_add_exact(c, t, sign, S, X);
   return pz_round(sign, S, X);
+}
+
+static __device__ __forceinline__ pz pz_add_inband(const pz_rtab *tab, pz c, pz t) {
+  uint32_t sign, X;
+  int S;
+  pz_add_exact(c, t, sign, S, X);
+  return pz_round_inband(tab, sign, S, X);
 }
 
 static __device__ __forceinline__ pz pz_add_tab(const pz_rtab *tab, pz c, pz t) {

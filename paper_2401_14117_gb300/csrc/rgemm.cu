@@ -36,6 +36,8 @@ constexpr int TM = 4, TN = 4;
 constexpr int NT = 512;  // (BM / TM) * (BN / TN)
 constexpr int GM = BM / TM;
 constexpr int64_t kGroupM = 16;  // row tiles per group of the launch order
+constexpr int kOpBand = 40;       // operand scales of the in-band fast path
+constexpr int kCBand = 80;        // starting C scales of the in-band fast path
 static_assert((BM / TM) * (BN / TN) == NT, "thread tile");
 
 template <int TRI>
@@ -54,6 +56,7 @@ rgemm_kernel(int64_t M, int64_t N, int64_t K, uint32_t alpha,
   __shared__ int rowNaR[BM];
   __shared__ int colNaR[BN];
   __shared__ pz_rtab rtab[256];
+  __shared__ pz_rtab rtab_in[256];
 
   const int tid = threadIdx.x;
   const int tm = tid % GM;  // row group: rows tm*TM .. +TM-1
@@ -76,12 +79,28 @@ rgemm_kernel(int64_t M, int64_t N, int64_t K, uint32_t alpha,
   const bool all_nar = beta == PZ_NAR_BITS || (alpha == PZ_NAR_BITS && K > 0);
   for (int i = tid; i < BM; i += NT) rowNaR[i] = 0;
   for (int j = tid; j < BN; j += NT) colNaR[j] = 0;
-  for (int i = tid; i < 256; i += NT) rtab[i] = pz_rtab_entry(i);
+  for (int i = tid; i < 256; i += NT) {
+    rtab[i] = pz_rtab_entry(i);
+    rtab_in[i] = pz_rtab_inband_entry(i);
+  }
 
   // Accumulators: padding elements (outside C or the triangle) start at 1
   // and are never stored; they only keep the warp on the fast path.
   pz acc[TM][TN];
   uint32_t c_nar = 0;  // bit i*TN+j: C_ij was NaR (beta != 0)
+  // In-band fast path.  While every operand t = alpha op(B)_lj and op(A)_il
+  // is zero or has its scale in [-40, 40], and every starting C value is zero
+  // or has its scale in [-80, 80], no rounding of the accumulation sees a
+  // scale outside [-108, 89], so none needs the test for the regimes of 28 or
+  // more bits.  Low end: every product and sum is a multiple of 2^-107 (a
+  // product has scale >= -80 and keeps at most 27 fraction bits; exact sums of
+  // multiples round to multiples), so a nonzero one is at least 2^-107.  High
+  // end: products are at most 2^82, and as rounding is monotone |c_k| <= B_k
+  // with B_0 < 2^81, B_(k+1) = round(B_k + 2^82), which stops growing once
+  // 2^82 is below half a unit in the last place: at 2^88 (f_s = 5 there),
+  // whatever K is.  The flag is cleared for good by the first tile with an
+  // operand outside the bounds.
+  bool in_band = true;
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
 #pragma unroll
@@ -103,12 +122,14 @@ rgemm_kernel(int64_t M, int64_t N, int64_t K, uint32_t alpha,
         }
       }
       acc[i][j] = v;
+      in_band &= pz_is_zero(v) || (v.s >= -kCBand && v.s <= kCBand);
     }
   }
 
   const int64_t kTot = (alpha == 0u) ? 0 : K;
   for (int64_t k0 = 0; k0 < kTot; k0 += BK) {
     __syncthreads();  // previous tile fully consumed
+    bool tile_ok = in_band;
 #pragma unroll
     for (int q = 0; q < (BM * BK) / NT; ++q) {
       int e = tid + q * NT;
@@ -125,6 +146,7 @@ rgemm_kernel(int64_t M, int64_t N, int64_t K, uint32_t alpha,
           v = pz_decode(w);
         }
       }
+      tile_ok &= pz_is_zero(v) || (v.s >= -kOpBand && v.s <= kOpBand);
       As[c][r] = v;
     }
 #pragma unroll
@@ -145,23 +167,41 @@ rgemm_kernel(int64_t M, int64_t N, int64_t K, uint32_t alpha,
           if (alpha != PZ_ONE_BITS && !all_nar) v = pz_mul_fast(pz_decode(alpha), v);
         }
       }
+      tile_ok &= pz_is_zero(v) || (v.s >= -kOpBand && v.s <= kOpBand);
       Bs[r][c] = v;
     }
-    __syncthreads();
+    in_band = __syncthreads_and(tile_ok) && in_band;
 
     const int kend = (int)min64(BK, K - k0);
+    if (in_band) {  // uniform over the CTA
 #pragma unroll 1
-    for (int kk = 0; kk < kend; ++kk) {
-      pz a[TM], b[TN];
+      for (int kk = 0; kk < kend; ++kk) {
+        pz a[TM], b[TN];
 #pragma unroll
-      for (int i = 0; i < TM; ++i) a[i] = As[kk][tm * TM + i];
+        for (int i = 0; i < TM; ++i) a[i] = As[kk][tm * TM + i];
 #pragma unroll
-      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tn * TN + j];
+        for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tn * TN + j];
 #pragma unroll
-      for (int i = 0; i < TM; ++i) {
+        for (int i = 0; i < TM; ++i) {
 #pragma unroll
-        for (int j = 0; j < TN; ++j)
-          acc[i][j] = pz_add_tab(rtab, acc[i][j], pz_mul_tab(rtab, b[j], a[i]));
+          for (int j = 0; j < TN; ++j)
+            acc[i][j] = pz_add_inband(rtab_in, acc[i][j], pz_mul_inband(rtab_in, b[j], a[i]));
+        }
+      }
+    } else {
+#pragma unroll 1
+      for (int kk = 0; kk < kend; ++kk) {
+        pz a[TM], b[TN];
+#pragma unroll
+        for (int i = 0; i < TM; ++i) a[i] = As[kk][tm * TM + i];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tn * TN + j];
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+#pragma unroll
+          for (int j = 0; j < TN; ++j)
+            acc[i][j] = pz_add_tab(rtab, acc[i][j], pz_mul_tab(rtab, b[j], a[i]));
+        }
       }
     }
   }

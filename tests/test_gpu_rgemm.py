@@ -70,6 +70,46 @@ def test_grouped_launch_order_and_remainder(ta, tb, m):
     assert_same(run_gpu(ta, tb, MONE, A, B, ONE, C), oracle.rgemm(ta, tb, MONE, A, B, ONE, C))
 
 
+def _pow2_words(rng, shape, lo, hi):
+    """Posit words of +-(1 + f) 2^e with e uniform in [lo, hi] (exact doubles)."""
+    e = rng.integers(lo, hi + 1, size=shape)
+    f = rng.integers(0, 1 << 20, size=shape) / float(1 << 20)
+    sgn = rng.choice([-1.0, 1.0], size=shape)
+    return oracle.from_double_array(sgn * (1.0 + f) * np.exp2(e.astype(np.float64)))
+
+
+@pytest.mark.parametrize("case", ["edge_high", "edge_low", "switch_mid_k", "c_out_of_band"])
+def test_in_band_fast_path_edges(case):
+    """The kernel skips the test for the long-regime band while all operands
+    have scales in [-40, 40] and C in [-80, 80]: sums pushed to 2^88 by
+    scale-40 operands, products at 2^-80 that cancel, a tile in the middle of
+    K with an operand outside the bounds (the rest of K is then checked), and
+    a starting C outside the bounds."""
+    rng = np.random.default_rng({"edge_high": 1, "edge_low": 2, "switch_mid_k": 3,
+                                 "c_out_of_band": 4}[case])
+    m, n, k = 150, 70, 700
+    if case == "edge_high":
+        A = _pow2_words(rng, (m, k), 39, 40)
+        B = oracle.from_double_array(np.abs(oracle.to_double_array(_pow2_words(rng, (k, n), 39, 40))))
+        A = oracle.from_double_array(np.abs(oracle.to_double_array(A)))
+        C = _pow2_words(rng, (m, n), 79, 80)
+    elif case == "edge_low":
+        A = _pow2_words(rng, (m, k), -40, -39)
+        B = _pow2_words(rng, (k, n), -40, -39)
+        C = _pow2_words(rng, (m, n), -80, -79)
+    elif case == "switch_mid_k":
+        A = _pow2_words(rng, (m, k), -20, 20)
+        B = _pow2_words(rng, (k, n), -20, 20)
+        A[17, 333] = oracle.from_double(2.0 ** 70)
+        C = words((m, n), 5)
+    else:
+        A = _pow2_words(rng, (m, k), -20, 20)
+        B = _pow2_words(rng, (k, n), -20, 20)
+        C = words((m, n), 6)
+        C[3, 4] = oracle.from_double(2.0 ** 90)
+    assert_same(run_gpu("N", "N", ONE, A, B, ONE, C), oracle.rgemm("N", "N", ONE, A, B, ONE, C))
+
+
 def test_special_values_inside_matrices():
     """Zeros, NaR, huge and tiny entries: the zero/NaR sentinels and the
     exponent-truncated rounding band inside the GEMM."""
