@@ -153,12 +153,12 @@ static __device__ __forceinline__ pz_rtab pz_rtab_entry(int i) {
   return e;
 }
 
-// Table for operands known to stay inside the fast band (see pz_round_inband):
-// the same constants, except that every scale outside it gets q = 30, which
-// leaves a zero significand zero (the only thing that can index those rows
-// then is the zero scale, clamped to row 255).
+// Table for values known to stay inside the fast band (see pz_round_inband),
+// indexed by the low 8 bits of the scale: row i holds the constants of the
+// scale (int8_t)i, and the rows of scales outside the band get q = 30.  A
+// zero (significand 0) may land on any row: every row rounds 0 to 0.
 static __device__ __forceinline__ pz_rtab pz_rtab_inband_entry(int i) {
-  pz_rtab e = pz_rtab_entry(i);
+  pz_rtab e = pz_rtab_entry(((i ^ 128) - 128) + 128);
   if (e.q > 31u) {
     e.keep = 0xC0000000u; e.hm1 = (1u << 29) - 1u; e.q = 30u;
   }
@@ -170,7 +170,7 @@ static __device__ __forceinline__ pz_rtab pz_rtab_inband_entry(int i) {
 // the table of pz_rtab_inband_entry.
 static __device__ __forceinline__ pz pz_round_inband(const pz_rtab *tab, uint32_t sign, int S,
                                                      uint32_t X) {
-  const pz_rtab e = tab[min((unsigned)(S + 128), 255u)];
+  const pz_rtab e = tab[S & 255];
   uint32_t lsb = (X >> e.q) & 1u;
   uint32_t r = (X + e.hm1 + lsb) & e.keep;
   uint32_t c = r >> 31;
@@ -278,10 +278,40 @@ static __device__ __forceinline__ pz pz_add_fast(pz c, pz t) {
   return pz_round(sign, S, X);
 }
 
+// pz_add_exact with clamping shifts instead of capping the alignment at 31
+// (the same value: a shift of 32 or more moves every bit into the jam).
+static __device__ __forceinline__ void pz_add_exact_clamp(pz c, pz t, uint32_t &sign, int &Sout,
+                                                          uint32_t &Xout) {
+  bool sw = t.s > c.s;
+  int SL = sw ? t.s : c.s;
+  int SS = sw ? c.s : t.s;
+  uint32_t mL = sw ? t.m : c.m;
+  uint32_t mS = sw ? c.m : t.m;
+  uint32_t d = (uint32_t)(SL - SS);
+  uint32_t magL = mL & 0x7FFFFFFFu;
+  uint32_t magS = mS & 0x7FFFFFFFu;
+  uint32_t shv = __funnelshift_rc(magS, 0u, d);   // magS >> d, 0 from 32 on
+  uint32_t lost = __funnelshift_rc(0u, magS, d);  // the bits shifted out
+  shv |= min(lost, 1u);
+  uint32_t sub = (mL ^ mS) >> 31;
+  uint32_t R = sub ? (magL - shv) : (magL + shv);
+  uint32_t neg = sub & (R >> 31);  // difference went negative (d = 0 only)
+  R = neg ? (0u - R) : R;
+  uint32_t sgn = (mL & 0x80000000u) ^ (neg << 31);
+  int lz = __clz(R);
+  int sft = lz - 1;  // left shift putting the leading one at bit 30
+  uint32_t X = sft >= 0 ? (R << sft) : ((R >> 1) | (R & 1u));
+  int S = SL - sft;
+  S = (R == 0u) ? PZ_SZERO : S;  // exact cancellation
+  sign = sgn;
+  Sout = S;
+  Xout = X;
+}
+
 static __device__ __forceinline__ pz pz_add_inband(const pz_rtab *tab, pz c, pz t) {
   uint32_t sign, X;
   int S;
-  pz_add_exact(c, t, sign, S, X);
+  pz_add_exact_clamp(c, t, sign, S, X);
   return pz_round_inband(tab, sign, S, X);
 }
 
