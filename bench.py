@@ -11,11 +11,12 @@ Under torchrun each rank runs its own independent problem (weak scaling, no
 collective); value = ops of all ranks / max time over ranks.
 
 The line also carries:
-  roofline      integer-issue roofline of the rgemm kernel: warp instructions
-                issued per second (instructions per launch from ncu's
-                smsp__inst_executed.sum, scaled per multiply-add) against
-                SMs x 4 schedulers x max SM clock; traffic = DRAM bytes of
-                one 8192^3 launch from the same ncu capture
+  roofline      integer-ALU-pipe roofline of the rgemm kernel: ALU-pipe warp
+                instructions per second (per multiply-add from ncu's
+                sm__inst_executed_pipe_alu.sum, times M N K, over the launch
+                time) against SMs x 4 schedulers x 0.5 x max SM clock; the
+                issue-slot figures ride along; traffic = DRAM bytes of one
+                8192^3 launch from an ncu capture
   e2e           the same metric measured with host buffers: host->device copy
                 of A and B, the call, device->host copy of C, every step
   cpu_baseline  the CPU oracle (plain C, OpenMP) on a bounded sample of the
@@ -38,15 +39,20 @@ METRIC = "Posit(32,2) Rgemm/Rgetrf Gflops vs INT-issue roofline; served-solve p5
 UNIT = "Gflops"
 ONE = 0x40000000
 
-# Warp instructions the rgemm kernel issues per posit multiply-add:
-# smsp__inst_executed.sum / (M N K) of one ncu capture of one launch of the
-# current kernel on the default workload (NN 8192^3, uniform [-1,1]:
-# 1.49425e12 / 5.4976e11; at 2048^3 the same kernel gives 2.7188).  The
-# count is set by the inner loop, so it scales with M N K.
-INST_PER_MAC = 2.7180
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of that same
-# captured 8192^3 launch: 4.96 GB read + 0.42 GB written.
-TRAFFIC_8192 = 4.96e9 + 0.41894e9
+# Per posit multiply-add of the rgemm kernel, from one ncu capture of one
+# launch of the current kernel (NN, uniform [-1,1]; the counts are set by the
+# inner loop, so they scale with M N K): integer-ALU-pipe warp instructions
+# (sm__inst_executed_pipe_alu.sum / M N K) and all warp instructions
+# (smsp__inst_executed.sum / M N K).
+ALU_INST_PER_MAC = 1.5015  # 8.25440e11 / 5.49756e11 (NN 8192^3)
+INST_PER_MAC = 2.0018      # 1.10052e12 / 5.49756e11
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one captured
+# 8192^3 launch.
+TRAFFIC_8192 = 4.96e9 + 0.42048e9
+# The kernel is bound by the integer ALU pipe: 16 lanes per scheduler, i.e.
+# 0.5 warp instruction per clock per scheduler (the rate at which ncu's
+# sm__inst_executed_pipe_alu.avg.pct_of_peak_sustained_active reads 100 %).
+ALU_WARP_INST_PER_CLK = 0.5
 SM_COUNT = 152
 SCHEDULERS_PER_SM = 4
 
@@ -334,20 +340,25 @@ def run_ours(args):
 
     # ---------------------------------------------------------- roofline
     peak_clock = clocks.get("sm_max_mhz") or 2070.0
-    peak = SM_COUNT * SCHEDULERS_PER_SM * peak_clock * 1e6 / 1e9  # G warp-inst/s
     macs = m * n * k
-    if INST_PER_MAC is not None:
-        achieved = INST_PER_MAC * macs / (launch_ms / 1e3) / 1e9
-        frac = achieved / peak
-    else:
-        achieved = frac = None
+    launch_s = launch_ms / 1e3
+    # bound: the integer ALU pipe (G warp instructions per second)
+    peak = SM_COUNT * SCHEDULERS_PER_SM * ALU_WARP_INST_PER_CLK * peak_clock * 1e6 / 1e9
+    achieved = ALU_INST_PER_MAC * macs / launch_s / 1e9
+    # issue slots, for context: 1 warp instruction per clock per scheduler
+    issue_peak = SM_COUNT * SCHEDULERS_PER_SM * peak_clock * 1e6 / 1e9
+    issue = INST_PER_MAC * macs / launch_s / 1e9
     traffic = TRAFFIC_8192 if (m, n, k) == (8192, 8192, 8192) else None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gwarp-inst/s",
-                "frac": frac, "traffic": traffic, "traffic_unit": "bytes per launch",
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "G ALU-pipe warp-inst/s", "frac": achieved / peak,
+                "traffic": traffic, "traffic_unit": "bytes per launch",
                 "algorithmic_bytes": 4.0 * (m * k + k * n + m * n),
-                "kernel": "rgemm_kernel<false,false,0>",
-                "launch_ms": launch_ms, "inst_per_mac": INST_PER_MAC,
-                "peak_basis": f"{SM_COUNT} SMs x {SCHEDULERS_PER_SM} schedulers x 1 warp-inst/clk x {peak_clock:.0f} MHz"}
+                "kernel": "rgemm_kernel<false,false,0>", "launch_ms": launch_ms,
+                "alu_inst_per_mac": ALU_INST_PER_MAC, "inst_per_mac": INST_PER_MAC,
+                "peak_basis": (f"{SM_COUNT} SMs x {SCHEDULERS_PER_SM} schedulers x "
+                               f"{ALU_WARP_INST_PER_CLK} ALU-pipe warp-inst/clk x {peak_clock:.0f} MHz"),
+                "issue": {"achieved": issue, "peak": issue_peak, "frac": issue / issue_peak,
+                          "unit": "G warp-inst/s"}}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max_ms / args.steps,

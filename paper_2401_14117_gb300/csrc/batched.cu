@@ -71,14 +71,31 @@ __device__ __forceinline__ pz mul_any(const pz_rtab *tab, pz a, pz b) {
   return FAST ? pz_mul_tab(tab, a, b) : pz_mul(a, b);
 }
 
+// In-band steps (tables of pz_rtab_inband_entry): one rounded operation whose
+// operands are zero or have scales in [-40, 40] (the reciprocal of such a
+// pivot: [-41, 40]) never leaves the scales [-107, 82], so it needs no test
+// for the regimes of 28 or more bits.  Each column checks that every value
+// it is about to use is in band: the trailing entries (checked when the
+// previous column updated them) and the scaled column (checked here).
+__device__ __forceinline__ bool out_of_band(pz v) {
+  return !pz_is_zero(v) && (v.s < -40 || v.s > 40);
+}
+
+__device__ __forceinline__ pz sub_mul_inband(const pz_rtab *tab, pz x, pz a, pz b) {
+  const pz p = pz_mul_inband(tab, a, b);
+  return pz_add_inband(tab, x, pz{p.s, p.m ^ 0x80000000u});
+}
+
 // LU with partial pivoting of the decoded n x n matrix M (column-major, ld n).
 // The rank-1 update runs with the lanes of a warp on consecutive rows and the
 // warps on columns.
 template <bool FAST>
-__device__ int lu_decoded(pz *M, int n, int32_t *ipiv, Key *red, pz *sh, const pz_rtab *tab) {
+__device__ int lu_decoded(pz *M, int n, int32_t *ipiv, Key *red, pz *sh, const pz_rtab *tab,
+                          const pz_rtab *tab_in, bool ib) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   int info = 0;
+  bool oob = false;
   for (int c = 0; c < n; ++c) {
     uint64_t best = 0;
     int brow = 0x7FFFFFFF;
@@ -104,26 +121,44 @@ __device__ int lu_decoded(pz *M, int n, int32_t *ipiv, Key *red, pz *sh, const p
       if (tid == 0) sh[0] = pz_div(pz_one(), M[c + (size_t)c * n]);
       __syncthreads();
       const pz r = sh[0];
-      for (int i = c + 1 + tid; i < n; i += nt)
-        M[i + (size_t)c * n] = mul_any<FAST>(tab, M[i + (size_t)c * n], r);
+      for (int i = c + 1 + tid; i < n; i += nt) {
+        pz *x = &M[i + (size_t)c * n];
+        *x = (FAST && ib) ? pz_mul_inband(tab_in, *x, r) : mul_any<FAST>(tab, *x, r);
+        oob |= out_of_band(*x);
+      }
     }
-    __syncthreads();
+    const bool any_oob = __syncthreads_or(oob);  // every thread reaches the barrier
+    const bool ib_update = FAST && ib && !any_oob;
+    oob = false;
     const pz *lc = M + (size_t)c * n;
     for (int k = c + 1 + warp; k < n; k += nw) {
       pz *col = M + (size_t)k * n;
       const pz u = col[c];
-      for (int i = c + 1 + lane; i < n; i += 32) col[i] = sub_mul<FAST>(tab, col[i], lc[i], u);
+      if (ib_update) {
+        for (int i = c + 1 + lane; i < n; i += 32) {
+          col[i] = sub_mul_inband(tab_in, col[i], lc[i], u);
+          oob |= out_of_band(col[i]);
+        }
+      } else {
+        for (int i = c + 1 + lane; i < n; i += 32) {
+          col[i] = sub_mul<FAST>(tab, col[i], lc[i], u);
+          oob |= out_of_band(col[i]);
+        }
+      }
     }
-    __syncthreads();
+    ib = !__syncthreads_or(oob);
+    oob = false;
   }
   return info;
 }
 
 // Cholesky (lower) of the decoded matrix; returns info.
 template <bool FAST>
-__device__ int chol_decoded(pz *M, int n, pz *sh, const pz_rtab *tab) {
+__device__ int chol_decoded(pz *M, int n, pz *sh, const pz_rtab *tab, const pz_rtab *tab_in,
+                            bool ib) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  bool oob = false;
   for (int j = 0; j < n; ++j) {
     pz d = M[j + (size_t)j * n];
     if (pz_is_nar(d) || pz_is_zero(d) || (d.m >> 31)) return j + 1;
@@ -135,17 +170,33 @@ __device__ int chol_decoded(pz *M, int n, pz *sh, const pz_rtab *tab) {
     __syncthreads();
     if (tid == 0) M[j + (size_t)j * n] = sh[0];
     const pz r = sh[1];
-    for (int i = j + 1 + tid; i < n; i += nt)
-      M[i + (size_t)j * n] = mul_any<FAST>(tab, M[i + (size_t)j * n], r);
-    __syncthreads();
+    for (int i = j + 1 + tid; i < n; i += nt) {
+      pz *x = &M[i + (size_t)j * n];
+      *x = (FAST && ib) ? pz_mul_inband(tab_in, *x, r) : mul_any<FAST>(tab, *x, r);
+      oob |= out_of_band(*x);
+    }
+    const bool any_oob = __syncthreads_or(oob);  // every thread reaches the barrier
+    const bool ib_update = FAST && ib && !any_oob;
+    oob = false;
     // a_ik -= l_ij l_kj for j < k <= i: column k from row k down
     const pz *lj = M + (size_t)j * n;
     for (int k = j + 1 + warp; k < n; k += nw) {
       pz *col = M + (size_t)k * n;
       const pz u = lj[k];
-      for (int i = k + lane; i < n; i += 32) col[i] = sub_mul<FAST>(tab, col[i], lj[i], u);
+      if (ib_update) {
+        for (int i = k + lane; i < n; i += 32) {
+          col[i] = sub_mul_inband(tab_in, col[i], lj[i], u);
+          oob |= out_of_band(col[i]);
+        }
+      } else {
+        for (int i = k + lane; i < n; i += 32) {
+          col[i] = sub_mul<FAST>(tab, col[i], lj[i], u);
+          oob |= out_of_band(col[i]);
+        }
+      }
     }
-    __syncthreads();
+    ib = !__syncthreads_or(oob);
+    oob = false;
   }
   return 0;
 }
@@ -154,9 +205,11 @@ __device__ int chol_decoded(pz *M, int n, pz *sh, const pz_rtab *tab) {
 // transposed mirror of chol_decoded: row j is scaled, the trailing upper
 // triangle updated.
 template <bool FAST>
-__device__ int chol_decoded_upper(pz *M, int n, pz *sh, const pz_rtab *tab, pz *row) {
+__device__ int chol_decoded_upper(pz *M, int n, pz *sh, const pz_rtab *tab, pz *row,
+                                  const pz_rtab *tab_in, bool ib) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  bool oob = false;
   for (int j = 0; j < n; ++j) {
     pz d = M[j + (size_t)j * n];
     if (pz_is_nar(d) || pz_is_zero(d) || (d.m >> 31)) return j + 1;
@@ -169,18 +222,33 @@ __device__ int chol_decoded_upper(pz *M, int n, pz *sh, const pz_rtab *tab, pz *
     if (tid == 0) M[j + (size_t)j * n] = sh[0];
     const pz r = sh[1];
     for (int k = j + 1 + tid; k < n; k += nt) {
-      const pz v = mul_any<FAST>(tab, M[j + (size_t)k * n], r);
+      const pz a = M[j + (size_t)k * n];
+      const pz v = (FAST && ib) ? pz_mul_inband(tab_in, a, r) : mul_any<FAST>(tab, a, r);
       M[j + (size_t)k * n] = v;
       row[k] = v;  // row j of U, contiguous
+      oob |= out_of_band(v);
     }
-    __syncthreads();
+    const bool any_oob = __syncthreads_or(oob);  // every thread reaches the barrier
+    const bool ib_update = FAST && ib && !any_oob;
+    oob = false;
     // a_ik -= u_ji u_jk for j < i <= k: column k from row j+1 to row k
     for (int k = j + 1 + warp; k < n; k += nw) {
       pz *col = M + (size_t)k * n;
       const pz u = row[k];
-      for (int i = j + 1 + lane; i <= k; i += 32) col[i] = sub_mul<FAST>(tab, col[i], row[i], u);
+      if (ib_update) {
+        for (int i = j + 1 + lane; i <= k; i += 32) {
+          col[i] = sub_mul_inband(tab_in, col[i], row[i], u);
+          oob |= out_of_band(col[i]);
+        }
+      } else {
+        for (int i = j + 1 + lane; i <= k; i += 32) {
+          col[i] = sub_mul<FAST>(tab, col[i], row[i], u);
+          oob |= out_of_band(col[i]);
+        }
+      }
     }
-    __syncthreads();
+    ib = !__syncthreads_or(oob);
+    oob = false;
   }
   return 0;
 }
@@ -291,8 +359,12 @@ __global__ void batched_kernel(const posit_problem *__restrict__ probs,
   __shared__ long long s_idx;
   __shared__ int s_nar;
   __shared__ pz_rtab rtab[256];
+  __shared__ pz_rtab rtab_in[256];
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int i = tid; i < 256; i += nt) rtab[i] = pz_rtab_entry(i);
+  for (int i = tid; i < 256; i += nt) {
+    rtab[i] = pz_rtab_entry(i);
+    rtab_in[i] = pz_rtab_inband_entry(i);
+  }
   pz *ws = workspace + (size_t)blockIdx.x * ws_elems_per_cta;
   for (;;) {
     if (tid == 0) {
@@ -314,15 +386,18 @@ __global__ void batched_kernel(const posit_problem *__restrict__ probs,
     const bool lower_only = P.kind == POSIT_CHOLESKY, upper_only = P.kind == POSIT_CHOLESKY_U;
     if (tid == 0) s_nar = 0;
     __syncthreads();
-    int nar = 0;
+    int nar = 0, oob = 0;
     for (int idx = tid; idx < n * n; idx += nt) {
       int i = idx % n, k = idx / n;
       bool skip = (lower_only && k > i) || (upper_only && k < i);
       const uint32_t w = skip ? 0u : P.A[i + (int64_t)k * P.lda];
       nar |= w == PZ_NAR_BITS;
-      M[idx] = pz_decode(w);
+      const pz v = pz_decode(w);
+      oob |= out_of_band(v);
+      M[idx] = v;
     }
     if (__syncthreads_or(nar) && tid == 0) s_nar = 1;
+    const bool ib0 = !__syncthreads_or(oob);
     for (int idx = tid; idx < n * nrhs; idx += nt) {
       int i = idx % n, c = idx / n;
       X[idx] = pz_decode(P.B[i + (int64_t)c * P.ldb]);
@@ -331,15 +406,16 @@ __global__ void batched_kernel(const posit_problem *__restrict__ probs,
     const bool fast = s_nar == 0;  // the matrix holds no NaR
     int info;
     if (P.kind == POSIT_LU) {
-      info = fast ? lu_decoded<true>(M, n, P.ipiv, red, sh, rtab)
-                  : lu_decoded<false>(M, n, P.ipiv, red, sh, rtab);
+      info = fast ? lu_decoded<true>(M, n, P.ipiv, red, sh, rtab, rtab_in, ib0)
+                  : lu_decoded<false>(M, n, P.ipiv, red, sh, rtab, rtab_in, false);
       getrs_decoded(M, n, P.ipiv, X, nrhs);
     } else if (P.kind == POSIT_CHOLESKY) {
-      info = fast ? chol_decoded<true>(M, n, sh, rtab) : chol_decoded<false>(M, n, sh, rtab);
+      info = fast ? chol_decoded<true>(M, n, sh, rtab, rtab_in, ib0)
+                  : chol_decoded<false>(M, n, sh, rtab, rtab_in, false);
       if (info == 0) potrs_decoded(M, n, X, nrhs, prod);
     } else {
-      info = fast ? chol_decoded_upper<true>(M, n, sh, rtab, prod)
-                  : chol_decoded_upper<false>(M, n, sh, rtab, prod);
+      info = fast ? chol_decoded_upper<true>(M, n, sh, rtab, prod, rtab_in, ib0)
+                  : chol_decoded_upper<false>(M, n, sh, rtab, prod, rtab_in, false);
       if (info == 0) potrs_decoded_upper(M, n, X, nrhs);
     }
     __syncthreads();

@@ -278,10 +278,15 @@ static __device__ __forceinline__ pz pz_add_fast(pz c, pz t) {
   return pz_round(sign, S, X);
 }
 
-// pz_add_exact with clamping shifts instead of capping the alignment at 31
-// (the same value: a shift of 32 or more moves every bit into the jam).
-static __device__ __forceinline__ void pz_add_exact_clamp(pz c, pz t, uint32_t &sign, int &Sout,
-                                                          uint32_t &Xout) {
+// pz_add_exact for the in-band path: clamping funnel shifts instead of
+// capping the alignment at 31 (a shift of 32 or more moves every bit into the
+// jam), normalisation through the form with the leading one at bit 31, and a
+// zero sum (count of leading zeros 32) placed 2^20 below the larger operand's
+// scale by a multiply-add instead of a select.  Same values as pz_add_exact
+// for the in-band operands; a zero keeps a significand of 0 and a scale far
+// below every nonzero in-band scale.
+static __device__ __forceinline__ void pz_add_exact_inband(pz c, pz t, uint32_t &sign, int &Sout,
+                                                           uint32_t &Xout) {
   bool sw = t.s > c.s;
   int SL = sw ? t.s : c.s;
   int SS = sw ? c.s : t.s;
@@ -297,21 +302,19 @@ static __device__ __forceinline__ void pz_add_exact_clamp(pz c, pz t, uint32_t &
   uint32_t R = sub ? (magL - shv) : (magL + shv);
   uint32_t neg = sub & (R >> 31);  // difference went negative (d = 0 only)
   R = neg ? (0u - R) : R;
-  uint32_t sgn = (mL & 0x80000000u) ^ (neg << 31);
-  int lz = __clz(R);
-  int sft = lz - 1;  // left shift putting the leading one at bit 30
-  uint32_t X = sft >= 0 ? (R << sft) : ((R >> 1) | (R & 1u));
-  int S = SL - sft;
-  S = (R == 0u) ? PZ_SZERO : S;  // exact cancellation
-  sign = sgn;
-  Sout = S;
-  Xout = X;
+  sign = (mL & 0x80000000u) ^ (neg << 31);
+  const int lz = __clz(R);
+  // lead at bit 31 (R << lz; 0 for R = 0), then back to bit 30 with the bit
+  // shifted out jammed (it can only be nonzero when lz = 0)
+  const uint32_t Y = __funnelshift_lc(0u, R, (uint32_t)lz);
+  Xout = (Y >> 1) | (Y & 1u);
+  Sout = (SL + 1 - lz) + (lz & 32) * -32768;
 }
 
 static __device__ __forceinline__ pz pz_add_inband(const pz_rtab *tab, pz c, pz t) {
   uint32_t sign, X;
   int S;
-  pz_add_exact_clamp(c, t, sign, S, X);
+  pz_add_exact_inband(c, t, sign, S, X);
   return pz_round_inband(tab, sign, S, X);
 }
 

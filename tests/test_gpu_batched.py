@@ -127,6 +127,38 @@ def test_batched_nar_and_no_right_hand_side():
         ps.restore(snap)
 
 
+def test_batched_in_band_switches():
+    """The factorisation drops the long-regime test while every value it is
+    about to use has a scale in [-40, 40]: Wilkinson's growth matrix leaves
+    that band mid-way (|u| doubles every column), a nearly rank-one SPD
+    matrix leaves it downwards (trailing entries near 2^-45), and a matrix
+    scaled by 2^45 starts outside it."""
+    n = 60
+    W = np.eye(n) - np.tril(np.ones((n, n)), -1)
+    W[:, -1] = 1.0
+    g = np.random.default_rng(9)
+    v = g.standard_normal(n)
+    R1 = np.outer(v, v) + 2.0 ** -45 * np.eye(n)
+    S = inputs.spd(n, 13) * 2.0 ** 45
+    Lbig = inputs.uniform((n, n), 14) * 2.0 ** 45
+    mats = [(L, W), (C, R1), (CU, R1), (C, S), (CU, S), (L, Lbig)]
+    kinds = np.array([k for k, _ in mats], np.int32)
+    ns = np.full(len(mats), n)
+    nrhs = np.ones(len(mats), np.int64)
+    ps, host = make_set(kinds, ns, nrhs, 31)
+    for i, (_, A64) in enumerate(mats):
+        A = oracle.from_double_array(A64)
+        B = host[i][1]
+        ps.set_problem(i, A, B)
+        host[i] = (A, B)
+    for plan in (PLANS[0], PLANS[3]):
+        snap = ps.snapshot()
+        ps.run(plan_of(*plan))
+        torch.cuda.synchronize()
+        check(ps, host)
+        ps.restore(snap)
+
+
 def test_batched_workload_sampled():
     """4096 problems, n log-uniform in [16, 512], half LU (uniform [-1,1]),
     half Cholesky (G G^T / n + I), 1 RHS: 160 problems (the largest ones
