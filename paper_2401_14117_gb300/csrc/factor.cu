@@ -428,19 +428,33 @@ constexpr int TRSM_T = 256;
 constexpr int TRSM_CHUNK = 16;
 constexpr int TRSM_MAXJB = 256;
 
+__device__ __forceinline__ bool trsm_out_of_band(pz v) {
+  return !pz_is_zero(v) && (v.s < -40 || v.s > 40);
+}
+
 __global__ void __launch_bounds__(TRSM_T)
 trsm_llu_kernel(uint32_t *__restrict__ A, int64_t lda, int64_t j, int jb, int64_t c0, int64_t c1) {
   __shared__ pz Ls[TRSM_CHUNK][TRSM_MAXJB];  // Ls[u][r] = l_{r, t0+u}
+  __shared__ pz_rtab tab_in[256];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t col = c0 + (int64_t)blockIdx.x * (TRSM_T / 32) + warp;
   const bool active = col < c1;  // warp-uniform
+  for (int i = tid; i < 256; i += TRSM_T) tab_in[i] = pz_rtab_inband_entry(i);
   uint32_t *cp = A + j + col * lda;
   pz xs[TRSM_MAXJB / 32];
+  bool oob = false;
 #pragma unroll
   for (int i = 0; i < TRSM_MAXJB / 32; ++i) {
     const int r = 32 * i + lane;
     xs[i] = (active && r < jb) ? pz_decode(cp[r]) : pz_zero();
+    oob |= trsm_out_of_band(xs[i]);
   }
+  // In-band steps: while l_{r,t}, u_t and the row's value are zero or have
+  // scales in [-40, 40], one rounded x - l u stays within the scales
+  // [-107, 82] and needs no test for the regimes of 28 or more bits (NaR is
+  // out of band).  The column's values are checked after every step, the
+  // chunk of L11 when it is loaded.
+  bool x_ok = !__any_sync(0xFFFFFFFFu, oob);
 #pragma unroll
   for (int i0 = 0; i0 < TRSM_MAXJB / 32; ++i0) {
     if (32 * i0 >= jb - 1) break;  // rows from 32*i0 on have nothing below them to update
@@ -449,12 +463,15 @@ trsm_llu_kernel(uint32_t *__restrict__ A, int64_t lda, int64_t j, int jb, int64_
       const int t0 = 32 * i0 + TRSM_CHUNK * h;
       if (t0 >= jb - 1) break;
       __syncthreads();
+      bool l_bad = false;
       for (int idx = tid; idx < TRSM_CHUNK * jb; idx += TRSM_T) {
         const int u = idx / jb, r = idx - u * jb;
         const int t = t0 + u;
-        Ls[u][r] = (r > t && t < jb) ? pz_decode(A[(j + r) + (j + t) * lda]) : pz_zero();
+        const pz v = (r > t && t < jb) ? pz_decode(A[(j + r) + (j + t) * lda]) : pz_zero();
+        l_bad |= trsm_out_of_band(v);
+        Ls[u][r] = v;
       }
-      __syncthreads();
+      const bool l_ok = !__syncthreads_or(l_bad);
       if (active) {
         const int un = min(TRSM_CHUNK, jb - 1 - t0);
         for (int u = 0; u < un; ++u) {
@@ -462,10 +479,29 @@ trsm_llu_kernel(uint32_t *__restrict__ A, int64_t lda, int64_t j, int jb, int64_
           const int owner = t & 31;
           const pz xt{__shfl_sync(0xFFFFFFFFu, xs[i0].s, owner),
                       __shfl_sync(0xFFFFFFFFu, xs[i0].m, owner)};
+          if (l_ok && x_ok) {  // warp-uniform
+            oob = false;
 #pragma unroll
-          for (int i = i0; i < TRSM_MAXJB / 32; ++i) {
-            const int r = 32 * i + lane;
-            if (r > t && r < jb) xs[i] = pz_sub(xs[i], pz_mul(Ls[u][r], xt));
+            for (int i = i0; i < TRSM_MAXJB / 32; ++i) {
+              const int r = 32 * i + lane;
+              if (r > t && r < jb) {
+                const pz p = pz_mul_inband(tab_in, Ls[u][r], xt);
+                xs[i] = pz_add_inband(tab_in, xs[i], pz{p.s, p.m ^ 0x80000000u});
+                oob |= trsm_out_of_band(xs[i]);
+              }
+            }
+            x_ok = !__any_sync(0xFFFFFFFFu, oob);
+          } else {
+            oob = false;
+#pragma unroll
+            for (int i = i0; i < TRSM_MAXJB / 32; ++i) {
+              const int r = 32 * i + lane;
+              if (r > t && r < jb) {
+                xs[i] = pz_sub(xs[i], pz_mul(Ls[u][r], xt));
+                oob |= trsm_out_of_band(xs[i]);
+              }
+            }
+            x_ok = !__any_sync(0xFFFFFFFFu, oob);
           }
         }
       }

@@ -64,6 +64,26 @@ def test_getrf_matches_oracle(m, n):
     assert np.array_equal(ipiv, ipo) and info == info_o
 
 
+@pytest.mark.parametrize("case", ["wilkinson", "scaled_up", "scaled_down"])
+def test_getrf_values_leaving_the_band(case):
+    """The trailing Rgemm and the U12 trsm round without the long-regime test
+    while their values have scales in [-40, 40]: Wilkinson's growth matrix
+    (|u| doubles every column, so the values leave the band part-way and
+    end saturated at maxpos), and
+    matrices scaled by 2^45 and 2^-45 (outside it from the start)."""
+    n = 600
+    if case == "wilkinson":
+        A64 = np.eye(n) - np.tril(np.ones((n, n)), -1)
+        A64[:, -1] = 1.0
+    else:
+        A64 = inputs.uniform((n, n), 42) * 2.0 ** (45 if case == "scaled_up" else -45)
+    A = oracle.from_double_array(A64)
+    F, ipiv, info = gpu_getrf(A)
+    Fo, ipo, info_o = oracle.rgetrf(A)
+    assert_same(F, Fo, "factors")
+    assert np.array_equal(ipiv, ipo) and info == info_o
+
+
 def test_getrf_zero_column_and_nar():
     A = words((300, 300), 5)
     A[:, 7] = 0
