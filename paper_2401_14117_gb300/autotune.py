@@ -23,7 +23,7 @@ CACHE_PATH = os.path.join(_HERE, "_build", "autotune_cache.json")
 def candidates():
     """Valid (threads, ctas_per_sm, smem_bytes) launch shapes."""
     out = []
-    for threads in (128, 256, 512):
+    for threads in (128, 256, 512, 1024):
         for ctas in (1, 2, 3, 4):
             if threads * ctas > THREADS_PER_SM:
                 continue

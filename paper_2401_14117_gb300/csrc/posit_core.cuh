@@ -344,21 +344,50 @@ static __device__ __forceinline__ pz pz_add(pz c, pz t) {
 
 static __device__ __forceinline__ pz pz_sub(pz c, pz t) { return pz_add(c, pz_neg(t)); }
 
-// a (/) b, one rounding.  Restoring division of the significands gives 32
-// quotient bits plus a remainder test for the jam bit.
+// floor(A * 2^31 / B) for significands A, B in [2^30, 2^31), and whether the
+// quotient is inexact.  The estimate comes from the correctly rounded float
+// reciprocal of B (relative error below 2^-22, so within 2^10 of the
+// quotient); one Newton-Raphson correction from the exact 64-bit remainder
+// brings it within 1; a final adjustment makes 0 <= remainder < B.
+static __device__ __forceinline__ uint32_t pz_sig_div(uint32_t A, uint32_t B, uint32_t &inexact) {
+  const uint64_t N = (uint64_t)A << 31;
+  const float rb = __frcp_rn(__uint2float_rn(B));
+  const float qf = fminf(__uint2float_rn(A) * rb * 2147483648.0f, 4294967040.0f);
+  uint32_t q = __float2uint_rz(qf);
+  int64_t R = (int64_t)(N - (uint64_t)q * B);
+  q += (uint32_t)__float2int_rz(__ll2float_rn(R) * rb);
+  R = (int64_t)(N - (uint64_t)q * B);
+  for (int i = 0; i < 4 && R < 0; ++i) { q -= 1u; R += B; }
+  for (int i = 0; i < 4 && R >= (int64_t)B; ++i) { q += 1u; R -= B; }
+  inexact = R != 0;
+  return q;
+}
+
+// floor(sqrt(N)) for N in [2^62, 2^64), and whether the root is inexact: an
+// estimate from the correctly rounded float reciprocal square root, one
+// Newton-Raphson correction from the exact 64-bit residual N - r^2, and a
+// final adjustment making 0 <= N - r^2 <= 2 r.
+static __device__ __forceinline__ uint32_t pz_sig_sqrt(uint64_t N, uint32_t &inexact) {
+  const float nf = __ull2float_rn(N);
+  const float y = __frsqrt_rn(nf);
+  uint32_t r = __float2uint_rz(fminf(nf * y, 4294967040.0f));
+  int64_t e = (int64_t)(N - (uint64_t)r * r);
+  r += (uint32_t)__float2int_rz(__ll2float_rn(e) * y * 0.5f);
+  e = (int64_t)(N - (uint64_t)r * r);
+  for (int i = 0; i < 4 && e < 0; ++i) { r -= 1u; e += 2 * (int64_t)r + 1; }
+  for (int i = 0; i < 4 && e > 2 * (int64_t)r; ++i) { e -= 2 * (int64_t)r + 1; r += 1u; }
+  inexact = e != 0;
+  return r;
+}
+
+// a (/) b, one rounding: 32 quotient bits of the significands plus the
+// inexact (jam) bit.
 static __device__ __noinline__ pz pz_div(pz a, pz b) {
   if (pz_is_nar(a) || pz_is_nar(b) || pz_is_zero(b)) return pz_nar();
   if (pz_is_zero(a)) return pz_zero();
   uint32_t A = a.m & 0x7FFFFFFFu, B = b.m & 0x7FFFFFFFu;  // both in [2^30, 2^31)
-  // quotient of (A / B) * 2^31, bit by bit (A / B lies in (1/2, 2))
-  uint64_t rem = A;
-  uint32_t q = 0;
-  for (int i = 31; i >= 0; --i) {
-    if (rem >= B) { rem -= B; q |= 1u << i; }
-    rem <<= 1;
-  }
-  // q = floor(A * 2^31 / B) in (2^30, 2^32)
-  uint32_t jam = rem != 0ull;
+  uint32_t jam;
+  const uint32_t q = pz_sig_div(A, B, jam);  // floor(A * 2^31 / B) in (2^30, 2^32)
   int S = a.s - b.s;
   uint32_t X;
   if (q >> 31) {
@@ -370,8 +399,8 @@ static __device__ __noinline__ pz pz_div(pz a, pz b) {
   return pz_round((a.m ^ b.m) & 0x80000000u, S, X);
 }
 
-// sqrt(a), one rounding.  Bit-by-bit integer square root of the significand
-// scaled to 64 bits, with a remainder test for the jam bit.
+// sqrt(a), one rounding: the integer square root of the significand scaled
+// to 64 bits, plus the inexact (jam) bit.
 static __device__ __noinline__ pz pz_sqrt(pz a) {
   if (pz_is_nar(a) || (a.m >> 31)) return pz_nar();
   if (pz_is_zero(a)) return pz_zero();
@@ -384,14 +413,9 @@ static __device__ __noinline__ pz pz_sqrt(pz a) {
   } else {
     N = (uint64_t)mag << 32;  // value = N * 2^(S - 62);     N in [2^62, 2^63)
   }
-  uint64_t r = 0;  // floor(sqrt(N)) < 2^32
-  for (int i = 31; i >= 0; --i) {
-    uint64_t t = r | (1ull << i);
-    if (t * t <= N) r = t;
-  }
-  uint32_t jam = (r * r) != N;
+  uint32_t jam;
+  const uint32_t r32 = pz_sig_sqrt(N, jam);  // floor(sqrt(N)) in [2^31, 2^32)
   // sqrt(value) = r * 2^((S - 62) / 2), r in [2^31, 2^32): lead at bit 31
-  uint32_t r32 = (uint32_t)r;
   uint32_t X = (r32 >> 1) | (r32 & 1u) | jam;
   return pz_round(0u, S >> 1, X);
 }

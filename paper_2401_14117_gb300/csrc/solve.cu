@@ -119,13 +119,23 @@ __global__ void __launch_bounds__(ST, 1) trsv_wave_kernel(TriArgs a) {
     const int64_t r0 = block_row0(a, J);
     const int nr = (int)min64(WBS, a.n - r0);
     if (J >= J0 && J < J1) {
+      // the diagonal tile, decoded into shared memory in one pass:
+      // at[r][t] = a(r0 + r, r0 + t)
+      for (int idx = tid; idx < WBS * WBS; idx += ST) {
+        int r, t;
+        if (a.trans) { t = idx % WBS; r = idx / WBS; } else { r = idx % WBS; t = idx / WBS; }
+        pz v = pz_zero();
+        if (r < nr && t < nr) v = pz_decode(tri_at(a, r0 + r, r0 + t));
+        at[r * WBS + t] = v;
+      }
+      __syncthreads();
       // solve the diagonal block in solve order
       pz *xb = xs + (size_t)(J - J0) * WBS * nrhs;
       for (int s = 0; s < nr; ++s) {
         const int t = a.backward ? (nr - 1 - s) : s;
         for (int c = tid; c < nrhs; c += ST) {
           pz x = xb[t * nrhs + c];
-          if (!a.unit) x = pz_div(x, pz_decode(tri_at(a, r0 + t, r0 + t)));
+          if (!a.unit) x = pz_div(x, at[t * WBS + t]);
           xb[t * nrhs + c] = x;
           a.B[(r0 + t) + c * a.ldb] = pz_to_bits(x);
         }
@@ -135,7 +145,7 @@ __global__ void __launch_bounds__(ST, 1) trsv_wave_kernel(TriArgs a) {
           int q = idx / nrhs, c = idx % nrhs;
           int r = a.backward ? (t - 1 - q) : (t + 1 + q);
           pz *x = &xb[r * nrhs + c];
-          *x = pz_sub(*x, pz_mul(pz_decode(tri_at(a, r0 + r, r0 + t)), xb[t * nrhs + c]));
+          *x = pz_sub(*x, pz_mul(at[r * WBS + t], xb[t * nrhs + c]));
         }
         __syncthreads();
       }
