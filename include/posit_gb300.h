@@ -187,7 +187,7 @@ POSIT_API int posit_rpotrs(char uplo, int64_t n, int64_t nrhs, const posit32_t *
  * this order (e.g. largest n first); NULL means 0, 1, 2, ...
  * max_n, max_nrhs: upper bounds over the problems (size the workspace).
  * plan: launch shape (any valid plan gives the same results):
- *   threads      threads per CTA (multiple of 32, <= 1024)
+ *   threads      threads per CTA (multiple of 32, <= 512)
  *   ctas_per_sm  persistent CTAs per SM
  *   smem_bytes   shared memory per CTA; a problem whose
  *                n*n + n*nrhs + n*max(nrhs, 1) decoded elements (8 bytes

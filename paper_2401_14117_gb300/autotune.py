@@ -14,7 +14,7 @@ import os
 
 SMEM_PER_SM = 228 * 1024          # GB300 shared memory per SM
 SMEM_PER_CTA_MAX = 227 * 1024
-THREADS_PER_SM = 2048
+THREADS_PER_SM = 512   # the batched kernel holds 128 registers per thread
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE_PATH = os.path.join(_HERE, "_build", "autotune_cache.json")
@@ -23,7 +23,7 @@ CACHE_PATH = os.path.join(_HERE, "_build", "autotune_cache.json")
 def candidates():
     """Valid (threads, ctas_per_sm, smem_bytes) launch shapes."""
     out = []
-    for threads in (128, 256, 512, 1024):
+    for threads in (128, 256, 512):
         for ctas in (1, 2, 3, 4):
             if threads * ctas > THREADS_PER_SM:
                 continue

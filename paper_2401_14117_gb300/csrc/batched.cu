@@ -86,9 +86,101 @@ __device__ __forceinline__ pz sub_mul_inband(const pz_rtab *tab, pz x, pz a, pz 
   return pz_add_inband(tab, x, pz{p.s, p.m ^ 0x80000000u});
 }
 
-// LU with partial pivoting of the decoded n x n matrix M (column-major, ld n).
-// The rank-1 update runs with the lanes of a warp on consecutive rows and the
-// warps on columns.
+// ---------------------------------------------------------------------------
+// Blocked factorisations inside one CTA.  Panels of BW columns (rows for the
+// upper Cholesky) are factored column by column; the rest of the matrix is
+// then brought up to date by a register-tiled update in which every element
+// receives the panel's BW terms in ascending order, exactly as the unblocked
+// algorithm orders them, so the result is the same for every panel width.
+// ---------------------------------------------------------------------------
+constexpr int BW = 16;             // panel width
+constexpr int TTM = 4, TTN = 2;    // register tile of the trailing update
+
+// M(r, c) -= sum_{t < kw} l(r, t) u(t, c), t ascending, for rows [r0, r1) and
+// columns [c0, c1) (tri 1: only c <= r; tri 2: only r <= c), with
+// l(r, t) = L[(r - r0) * li + t * lt] and u(t, c) = U[t * su + (c - c0) * sk].
+// ib: the operands and the starting values are zero or have scales in
+// [-40, 40]; then, as in Rgemm, no rounding of the chain can reach the
+// regimes of 28 or more bits.  Returns (after a barrier) whether any updated
+// value is outside [-40, 40].
+template <bool FAST>
+__device__ bool trailing_update(pz *M, int n, int r0, int r1, int c0, int c1, const pz *L, int li,
+                                int lt, const pz *U, int su, int sk, int kw, int tri,
+                                const pz_rtab *tab, const pz_rtab *tab_in, bool ib) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int nr = r1 - r0, nc = c1 - c0;
+  bool oob = false;
+  if (nr > 0 && nc > 0 && kw > 0) {
+    const int rs = (nr + TTM - 1) / TTM;  // row stride of a tile: its rows are r0+tr+i*rs
+    const int ncol_t = (nc + TTN - 1) / TTN;
+    const int tiles = rs * ncol_t;
+    for (int tile = tid; tile < tiles; tile += nt) {
+      const int tr = tile % rs, tc = tile / rs;
+      int rr[TTM], cc[TTN];
+      bool ok[TTM][TTN];
+      pz acc[TTM][TTN];
+#pragma unroll
+      for (int i = 0; i < TTM; ++i) rr[i] = tr + i * rs;
+#pragma unroll
+      for (int j = 0; j < TTN; ++j) cc[j] = tc * TTN + j;
+      bool any = false;
+#pragma unroll
+      for (int i = 0; i < TTM; ++i)
+#pragma unroll
+        for (int j = 0; j < TTN; ++j) {
+          const int r = r0 + rr[i], c = c0 + cc[j];
+          ok[i][j] = rr[i] < nr && cc[j] < nc &&
+                     (tri == 0 || (tri == 1 ? c <= r : r <= c));
+          acc[i][j] = ok[i][j] ? M[r + (size_t)c * n] : pz_one();
+          any |= ok[i][j];
+        }
+      if (!any) continue;
+      for (int t = 0; t < kw; ++t) {
+        pz l[TTM], u[TTN];
+#pragma unroll
+        for (int i = 0; i < TTM; ++i)
+          l[i] = rr[i] < nr ? L[(size_t)rr[i] * li + (size_t)t * lt] : pz_one();
+#pragma unroll
+        for (int j = 0; j < TTN; ++j)
+          u[j] = cc[j] < nc ? U[(size_t)t * su + (size_t)cc[j] * sk] : pz_one();
+        if (FAST && ib) {
+#pragma unroll
+          for (int i = 0; i < TTM; ++i)
+#pragma unroll
+            for (int j = 0; j < TTN; ++j) acc[i][j] = sub_mul_inband(tab_in, acc[i][j], l[i], u[j]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < TTM; ++i)
+#pragma unroll
+            for (int j = 0; j < TTN; ++j) acc[i][j] = sub_mul<FAST>(tab, acc[i][j], l[i], u[j]);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < TTM; ++i)
+#pragma unroll
+        for (int j = 0; j < TTN; ++j)
+          if (ok[i][j]) {
+            M[(r0 + rr[i]) + (size_t)(c0 + cc[j]) * n] = acc[i][j];
+            oob |= out_of_band(acc[i][j]);
+          }
+    }
+  }
+  return __syncthreads_or(oob);
+}
+
+// Whether any element of the r x c block at P (element (i, j) at
+// P[i * si + j * sj]) is outside [-40, 40], after a barrier.
+__device__ bool block_out_of_band(const pz *P, int r, int c, int si, int sj) {
+  bool oob = false;
+  for (int idx = threadIdx.x; idx < r * c; idx += blockDim.x) {
+    const int i = idx % r, j = idx / r;
+    oob |= out_of_band(P[(size_t)i * si + (size_t)j * sj]);
+  }
+  return __syncthreads_or(oob);
+}
+
+// LU with partial pivoting of the decoded n x n matrix M (column-major, ld n),
+// blocked by BW columns.  ib: every entry starts in band.
 template <bool FAST>
 __device__ int lu_decoded(pz *M, int n, int32_t *ipiv, Key *red, pz *sh, const pz_rtab *tab,
                           const pz_rtab *tab_in, bool ib) {
@@ -96,159 +188,217 @@ __device__ int lu_decoded(pz *M, int n, int32_t *ipiv, Key *red, pz *sh, const p
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   int info = 0;
   bool oob = false;
-  for (int c = 0; c < n; ++c) {
-    uint64_t best = 0;
-    int brow = 0x7FFFFFFF;
-    for (int i = c + tid; i < n; i += nt) {
-      uint64_t k = abs_key(M[i + (size_t)c * n]);
-      if (key_better(k, i, best, brow)) { best = k; brow = i; }
-    }
-    Key w = block_argmax(best, brow, red);
-    const int p = w.r;
-    const bool zero = pz_is_zero(M[p + (size_t)c * n]);
-    if (tid == 0) ipiv[c] = p + 1;
-    if (zero) {
-      if (info == 0) info = c + 1;
-    } else {
-      if (p != c)
-        for (int k = tid; k < n; k += nt) {
-          pz t = M[c + (size_t)k * n];
-          M[c + (size_t)k * n] = M[p + (size_t)k * n];
-          M[p + (size_t)k * n] = t;
-        }
-      __syncthreads();
-      // after the swap the pivot sits at (c, c)
-      if (tid == 0) sh[0] = pz_div(pz_one(), M[c + (size_t)c * n]);
-      __syncthreads();
-      const pz r = sh[0];
-      for (int i = c + 1 + tid; i < n; i += nt) {
-        pz *x = &M[i + (size_t)c * n];
-        *x = (FAST && ib) ? pz_mul_inband(tab_in, *x, r) : mul_any<FAST>(tab, *x, r);
-        oob |= out_of_band(*x);
+  for (int p0 = 0; p0 < n; p0 += BW) {
+    const int pe = min(n, p0 + BW);  // panel columns [p0, pe)
+    // ---- the panel, column by column (in-panel updates only)
+    for (int c = p0; c < pe; ++c) {
+      uint64_t best = 0;
+      int brow = 0x7FFFFFFF;
+      for (int i = c + tid; i < n; i += nt) {
+        uint64_t k = abs_key(M[i + (size_t)c * n]);
+        if (key_better(k, i, best, brow)) { best = k; brow = i; }
       }
-    }
-    const bool any_oob = __syncthreads_or(oob);  // every thread reaches the barrier
-    const bool ib_update = FAST && ib && !any_oob;
-    oob = false;
-    const pz *lc = M + (size_t)c * n;
-    for (int k = c + 1 + warp; k < n; k += nw) {
-      pz *col = M + (size_t)k * n;
-      const pz u = col[c];
-      if (ib_update) {
-        for (int i = c + 1 + lane; i < n; i += 32) {
-          col[i] = sub_mul_inband(tab_in, col[i], lc[i], u);
-          oob |= out_of_band(col[i]);
-        }
+      Key w = block_argmax(best, brow, red);
+      const int p = w.r;
+      const bool zero = pz_is_zero(M[p + (size_t)c * n]);
+      if (tid == 0) ipiv[c] = p + 1;
+      if (zero) {
+        if (info == 0) info = c + 1;
       } else {
-        for (int i = c + 1 + lane; i < n; i += 32) {
-          col[i] = sub_mul<FAST>(tab, col[i], lc[i], u);
-          oob |= out_of_band(col[i]);
+        if (p != c)  // the whole rows, so the trailing columns are permuted too
+          for (int k = tid; k < n; k += nt) {
+            pz t = M[c + (size_t)k * n];
+            M[c + (size_t)k * n] = M[p + (size_t)k * n];
+            M[p + (size_t)k * n] = t;
+          }
+        __syncthreads();
+        // after the swap the pivot sits at (c, c)
+        if (tid == 0) sh[0] = pz_div(pz_one(), M[c + (size_t)c * n]);
+        __syncthreads();
+        const pz r = sh[0];
+        for (int i = c + 1 + tid; i < n; i += nt) {
+          pz *x = &M[i + (size_t)c * n];
+          *x = (FAST && ib) ? pz_mul_inband(tab_in, *x, r) : mul_any<FAST>(tab, *x, r);
+          oob |= out_of_band(*x);
         }
       }
+      const bool any_oob = __syncthreads_or(oob);  // every thread reaches the barrier
+      const bool ib_update = FAST && ib && !any_oob;
+      oob = false;
+      const pz *lc = M + (size_t)c * n;
+      for (int k = c + 1 + warp; k < pe; k += nw) {
+        pz *col = M + (size_t)k * n;
+        const pz u = col[c];
+        if (ib_update) {
+          for (int i = c + 1 + lane; i < n; i += 32) {
+            col[i] = sub_mul_inband(tab_in, col[i], lc[i], u);
+            oob |= out_of_band(col[i]);
+          }
+        } else {
+          for (int i = c + 1 + lane; i < n; i += 32) {
+            col[i] = sub_mul<FAST>(tab, col[i], lc[i], u);
+            oob |= out_of_band(col[i]);
+          }
+        }
+      }
+      // ib keeps describing the trailing entries the later panel columns use
+      ib = ib && !__syncthreads_or(oob) && !any_oob;
+      oob = false;
     }
-    ib = !__syncthreads_or(oob);
-    oob = false;
+    if (pe >= n) break;
+    // ---- U12: rows [p0, pe) of the columns right of the panel; one thread
+    // per column, t ascending for every row
+    for (int k = pe + tid; k < n; k += nt) {
+      pz *col = M + (size_t)k * n;
+      for (int r = p0 + 1; r < pe; ++r) {
+        pz x = col[r];
+        for (int t = p0; t < r; ++t) x = sub_mul<FAST>(tab, x, M[r + (size_t)t * n], col[t]);
+        col[r] = x;
+      }
+    }
+    __syncthreads();
+    // ---- A22 -= L21 U12 (K = pe - p0)
+    const bool ops_in = !block_out_of_band(M + pe + (size_t)p0 * n, n - pe, pe - p0, 1, n) &&
+                        !block_out_of_band(M + p0 + (size_t)pe * n, pe - p0, n - pe, 1, n);
+    const bool a22_oob = trailing_update<FAST>(M, n, pe, n, pe, n, M + pe + (size_t)p0 * n, 1, n,
+                                               M + p0 + (size_t)pe * n, 1, n, pe - p0, 0, tab,
+                                               tab_in, FAST && ib && ops_in);
+    ib = !a22_oob;
   }
   return info;
 }
 
-// Cholesky (lower) of the decoded matrix; returns info.
+// Cholesky (lower) of the decoded matrix, blocked by BW columns; returns info.
 template <bool FAST>
 __device__ int chol_decoded(pz *M, int n, pz *sh, const pz_rtab *tab, const pz_rtab *tab_in,
                             bool ib) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   bool oob = false;
-  for (int j = 0; j < n; ++j) {
-    pz d = M[j + (size_t)j * n];
-    if (pz_is_nar(d) || pz_is_zero(d) || (d.m >> 31)) return j + 1;
-    if (tid == 0) {
-      pz s = pz_sqrt(d);
-      sh[0] = s;
-      sh[1] = pz_div(pz_one(), s);
-    }
-    __syncthreads();
-    if (tid == 0) M[j + (size_t)j * n] = sh[0];
-    const pz r = sh[1];
-    for (int i = j + 1 + tid; i < n; i += nt) {
-      pz *x = &M[i + (size_t)j * n];
-      *x = (FAST && ib) ? pz_mul_inband(tab_in, *x, r) : mul_any<FAST>(tab, *x, r);
-      oob |= out_of_band(*x);
-    }
-    const bool any_oob = __syncthreads_or(oob);  // every thread reaches the barrier
-    const bool ib_update = FAST && ib && !any_oob;
-    oob = false;
-    // a_ik -= l_ij l_kj for j < k <= i: column k from row k down
-    const pz *lj = M + (size_t)j * n;
-    for (int k = j + 1 + warp; k < n; k += nw) {
-      pz *col = M + (size_t)k * n;
-      const pz u = lj[k];
-      if (ib_update) {
-        for (int i = k + lane; i < n; i += 32) {
-          col[i] = sub_mul_inband(tab_in, col[i], lj[i], u);
-          oob |= out_of_band(col[i]);
-        }
-      } else {
-        for (int i = k + lane; i < n; i += 32) {
-          col[i] = sub_mul<FAST>(tab, col[i], lj[i], u);
-          oob |= out_of_band(col[i]);
+  for (int p0 = 0; p0 < n; p0 += BW) {
+    const int pe = min(n, p0 + BW);
+    for (int j = p0; j < pe; ++j) {
+      pz d = M[j + (size_t)j * n];
+      if (pz_is_nar(d) || pz_is_zero(d) || (d.m >> 31)) {
+        // leave the trailing triangle as the unblocked algorithm does: with
+        // the updates of the panel's completed columns p0 .. j-1
+        if (pe < n)
+          trailing_update<FAST>(M, n, pe, n, pe, n, M + pe + (size_t)p0 * n, 1, n,
+                                M + pe + (size_t)p0 * n, n, 1, j - p0, 1, tab, tab_in, false);
+        return j + 1;
+      }
+      if (tid == 0) {
+        pz s = pz_sqrt(d);
+        sh[0] = s;
+        sh[1] = pz_div(pz_one(), s);
+      }
+      __syncthreads();
+      if (tid == 0) M[j + (size_t)j * n] = sh[0];
+      const pz r = sh[1];
+      for (int i = j + 1 + tid; i < n; i += nt) {
+        pz *x = &M[i + (size_t)j * n];
+        *x = (FAST && ib) ? pz_mul_inband(tab_in, *x, r) : mul_any<FAST>(tab, *x, r);
+        oob |= out_of_band(*x);
+      }
+      const bool any_oob = __syncthreads_or(oob);  // every thread reaches the barrier
+      const bool ib_update = FAST && ib && !any_oob;
+      oob = false;
+      // a_ik -= l_ij l_kj for the panel columns k in (j, pe), rows i >= k
+      const pz *lj = M + (size_t)j * n;
+      for (int k = j + 1 + warp; k < pe; k += nw) {
+        pz *col = M + (size_t)k * n;
+        const pz u = lj[k];
+        if (ib_update) {
+          for (int i = k + lane; i < n; i += 32) {
+            col[i] = sub_mul_inband(tab_in, col[i], lj[i], u);
+            oob |= out_of_band(col[i]);
+          }
+        } else {
+          for (int i = k + lane; i < n; i += 32) {
+            col[i] = sub_mul<FAST>(tab, col[i], lj[i], u);
+            oob |= out_of_band(col[i]);
+          }
         }
       }
+      ib = ib && !__syncthreads_or(oob) && !any_oob;
+      oob = false;
     }
-    ib = !__syncthreads_or(oob);
-    oob = false;
+    if (pe >= n) break;
+    // the trailing lower triangle: a_ik -= sum_t l_it l_kt, t ascending
+    const pz *L21 = M + pe + (size_t)p0 * n;
+    const bool ops_in = !block_out_of_band(L21, n - pe, pe - p0, 1, n);
+    const bool a22_oob = trailing_update<FAST>(M, n, pe, n, pe, n, L21, 1, n, L21, n, 1, pe - p0,
+                                               1, tab, tab_in, FAST && ib && ops_in);
+    ib = !a22_oob;
   }
   return 0;
 }
 
-// Cholesky (upper, A = U^T U) of the decoded matrix; returns info.  The
-// transposed mirror of chol_decoded: row j is scaled, the trailing upper
-// triangle updated.
+// Cholesky (upper, A = U^T U) of the decoded matrix, blocked by BW rows: the
+// transposed mirror of chol_decoded (row j is scaled, the trailing upper
+// triangle updated).  row: scratch of n elements for the scaled row.
 template <bool FAST>
 __device__ int chol_decoded_upper(pz *M, int n, pz *sh, const pz_rtab *tab, pz *row,
                                   const pz_rtab *tab_in, bool ib) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   bool oob = false;
-  for (int j = 0; j < n; ++j) {
-    pz d = M[j + (size_t)j * n];
-    if (pz_is_nar(d) || pz_is_zero(d) || (d.m >> 31)) return j + 1;
-    if (tid == 0) {
-      pz s = pz_sqrt(d);
-      sh[0] = s;
-      sh[1] = pz_div(pz_one(), s);
-    }
-    __syncthreads();
-    if (tid == 0) M[j + (size_t)j * n] = sh[0];
-    const pz r = sh[1];
-    for (int k = j + 1 + tid; k < n; k += nt) {
-      const pz a = M[j + (size_t)k * n];
-      const pz v = (FAST && ib) ? pz_mul_inband(tab_in, a, r) : mul_any<FAST>(tab, a, r);
-      M[j + (size_t)k * n] = v;
-      row[k] = v;  // row j of U, contiguous
-      oob |= out_of_band(v);
-    }
-    const bool any_oob = __syncthreads_or(oob);  // every thread reaches the barrier
-    const bool ib_update = FAST && ib && !any_oob;
-    oob = false;
-    // a_ik -= u_ji u_jk for j < i <= k: column k from row j+1 to row k
-    for (int k = j + 1 + warp; k < n; k += nw) {
-      pz *col = M + (size_t)k * n;
-      const pz u = row[k];
-      if (ib_update) {
-        for (int i = j + 1 + lane; i <= k; i += 32) {
-          col[i] = sub_mul_inband(tab_in, col[i], row[i], u);
-          oob |= out_of_band(col[i]);
-        }
-      } else {
-        for (int i = j + 1 + lane; i <= k; i += 32) {
-          col[i] = sub_mul<FAST>(tab, col[i], row[i], u);
-          oob |= out_of_band(col[i]);
+  for (int p0 = 0; p0 < n; p0 += BW) {
+    const int pe = min(n, p0 + BW);
+    for (int j = p0; j < pe; ++j) {
+      pz d = M[j + (size_t)j * n];
+      if (pz_is_nar(d) || pz_is_zero(d) || (d.m >> 31)) {
+        // the trailing triangle as the unblocked algorithm leaves it
+        if (pe < n)
+          trailing_update<FAST>(M, n, pe, n, pe, n, M + p0 + (size_t)pe * n, n, 1,
+                                M + p0 + (size_t)pe * n, 1, n, j - p0, 2, tab, tab_in, false);
+        return j + 1;
+      }
+      if (tid == 0) {
+        pz s = pz_sqrt(d);
+        sh[0] = s;
+        sh[1] = pz_div(pz_one(), s);
+      }
+      __syncthreads();
+      if (tid == 0) M[j + (size_t)j * n] = sh[0];
+      const pz r = sh[1];
+      for (int k = j + 1 + tid; k < n; k += nt) {
+        const pz a = M[j + (size_t)k * n];
+        const pz v = (FAST && ib) ? pz_mul_inband(tab_in, a, r) : mul_any<FAST>(tab, a, r);
+        M[j + (size_t)k * n] = v;
+        row[k] = v;  // row j of U, contiguous
+        oob |= out_of_band(v);
+      }
+      const bool any_oob = __syncthreads_or(oob);  // every thread reaches the barrier
+      const bool ib_update = FAST && ib && !any_oob;
+      oob = false;
+      // a_ik -= u_ji u_jk for the panel rows i in (j, pe), columns k >= i
+      for (int k = j + 1 + warp; k < n; k += nw) {
+        pz *col = M + (size_t)k * n;
+        const pz u = row[k];
+        const int ie = min(k + 1, pe);
+        if (ib_update) {
+          for (int i = j + 1 + lane; i < ie; i += 32) {
+            col[i] = sub_mul_inband(tab_in, col[i], row[i], u);
+            oob |= out_of_band(col[i]);
+          }
+        } else {
+          for (int i = j + 1 + lane; i < ie; i += 32) {
+            col[i] = sub_mul<FAST>(tab, col[i], row[i], u);
+            oob |= out_of_band(col[i]);
+          }
         }
       }
+      ib = ib && !__syncthreads_or(oob) && !any_oob;
+      oob = false;
     }
-    ib = !__syncthreads_or(oob);
-    oob = false;
+    if (pe >= n) break;
+    // the trailing upper triangle: a_ik -= sum_t u_ti u_tk for i <= k
+    const pz *U12 = M + p0 + (size_t)pe * n;  // u(t, c) at U12[t + (c - pe) * n]
+    const bool ops_in = !block_out_of_band(U12, pe - p0, n - pe, 1, n);
+    const bool a22_oob = trailing_update<FAST>(M, n, pe, n, pe, n, U12, n, 1, U12, 1, n, pe - p0,
+                                               2, tab, tab_in, FAST && ib && ops_in);
+    ib = !a22_oob;
   }
   return 0;
 }
@@ -348,7 +498,7 @@ __device__ void potrs_decoded(const pz *M, int n, pz *X, int nrhs, pz *prod) {
   }
 }
 
-__global__ void batched_kernel(const posit_problem *__restrict__ probs,
+__global__ void __launch_bounds__(512) batched_kernel(const posit_problem *__restrict__ probs,
                                const int32_t *__restrict__ order, int64_t count,
                                unsigned long long *counter, pz *workspace,
                                size_t ws_elems_per_cta, int smem_elems) {
@@ -475,7 +625,7 @@ using namespace posit;
 
 namespace {
 bool plan_ok(const posit_plan *p) {
-  return p && p->threads >= 32 && p->threads <= 1024 && (p->threads % 32) == 0 &&
+  return p && p->threads >= 32 && p->threads <= 512 && (p->threads % 32) == 0 &&
          p->ctas_per_sm >= 1 && p->ctas_per_sm <= 32 && p->smem_bytes >= 0 &&
          p->smem_bytes <= 232448;
 }
