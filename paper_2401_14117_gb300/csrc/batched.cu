@@ -242,7 +242,8 @@ __device__ int lu_decoded(pz *M, int n, int32_t *ipiv, Key *red, pz *sh, const p
         }
       }
       // ib keeps describing the trailing entries the later panel columns use
-      ib = ib && !__syncthreads_or(oob) && !any_oob;
+      const bool upd_oob = __syncthreads_or(oob);  // every thread reaches the barrier
+      ib = ib && !upd_oob && !any_oob;
       oob = false;
     }
     if (pe >= n) break;
@@ -258,8 +259,9 @@ __device__ int lu_decoded(pz *M, int n, int32_t *ipiv, Key *red, pz *sh, const p
     }
     __syncthreads();
     // ---- A22 -= L21 U12 (K = pe - p0)
-    const bool ops_in = !block_out_of_band(M + pe + (size_t)p0 * n, n - pe, pe - p0, 1, n) &&
-                        !block_out_of_band(M + p0 + (size_t)pe * n, pe - p0, n - pe, 1, n);
+    const bool l21_oob = block_out_of_band(M + pe + (size_t)p0 * n, n - pe, pe - p0, 1, n);
+    const bool u12_oob = block_out_of_band(M + p0 + (size_t)pe * n, pe - p0, n - pe, 1, n);
+    const bool ops_in = !l21_oob && !u12_oob;
     const bool a22_oob = trailing_update<FAST>(M, n, pe, n, pe, n, M + pe + (size_t)p0 * n, 1, n,
                                                M + p0 + (size_t)pe * n, 1, n, pe - p0, 0, tab,
                                                tab_in, FAST && ib && ops_in);
@@ -320,7 +322,8 @@ __device__ int chol_decoded(pz *M, int n, pz *sh, const pz_rtab *tab, const pz_r
           }
         }
       }
-      ib = ib && !__syncthreads_or(oob) && !any_oob;
+      const bool upd_oob = __syncthreads_or(oob);  // every thread reaches the barrier
+      ib = ib && !upd_oob && !any_oob;
       oob = false;
     }
     if (pe >= n) break;
@@ -389,7 +392,8 @@ __device__ int chol_decoded_upper(pz *M, int n, pz *sh, const pz_rtab *tab, pz *
           }
         }
       }
-      ib = ib && !__syncthreads_or(oob) && !any_oob;
+      const bool upd_oob = __syncthreads_or(oob);  // every thread reaches the barrier
+      ib = ib && !upd_oob && !any_oob;
       oob = false;
     }
     if (pe >= n) break;
