@@ -45,22 +45,25 @@ __device__ __forceinline__ bool tri_ok(int64_t i, int64_t j) {
   return TRI == TRI_FULL || (TRI == TRI_LOWER ? i >= j : i <= j);
 }
 
-template <bool TA, bool TB, int TRI>
+template <bool TA, bool TB, int TRI, int TMV>
 __global__ void __launch_bounds__(NT, 2)
 rgemm_kernel(int64_t M, int64_t N, int64_t K, uint32_t alpha,
              const uint32_t *__restrict__ A, int64_t lda,
              const uint32_t *__restrict__ B, int64_t ldb, uint32_t beta,
              uint32_t *__restrict__ C, int64_t ldc, const int32_t *__restrict__ abort_flag) {
-  __shared__ __align__(16) pz As[BK][BM];
+  constexpr int BMV = 32 * TMV;  // CTA rows: 32 row groups of TMV rows
+  constexpr int GMV = BMV / TMV;
+  static_assert(GMV * (BN / TN) == NT, "thread tile");
+  __shared__ __align__(16) pz As[BK][BMV];
   __shared__ __align__(16) pz Bs[BK][BN];
-  __shared__ int rowNaR[BM];
+  __shared__ int rowNaR[BMV];
   __shared__ int colNaR[BN];
   __shared__ pz_rtab rtab[256];
   __shared__ pz_rtab rtab_in[256];
 
   const int tid = threadIdx.x;
-  const int tm = tid % GM;  // row group: rows tm*TM .. +TM-1
-  const int tn = tid / GM;  // column group (one warp): cols tn*TN .. +TN-1
+  const int tm = tid % GMV;  // row group: rows tm*TMV .. +TMV-1
+  const int tn = tid / GMV;  // column group (one warp): cols tn*TN .. +TN-1
   // Grouped launch order (full matrices with more than kGroupM row tiles):
   // the grid is (kGroupM row tiles, column tiles, groups; the last group may
   // be partial), so consecutive CTAs take kGroupM row tiles by a run of
@@ -69,15 +72,15 @@ rgemm_kernel(int64_t M, int64_t N, int64_t K, uint32_t alpha,
   // read from L2 instead of each from DRAM.  Otherwise the grid is (row
   // tiles, column tiles, 1).
   const unsigned mt = blockIdx.z * (unsigned)kGroupM + blockIdx.x;
-  if (mt >= (unsigned)((M + BM - 1) / BM)) return;  // the last group may be partial
-  const int64_t m0 = (int64_t)mt * BM;
+  if (mt >= (unsigned)((M + BMV - 1) / BMV)) return;  // the last group may be partial
+  const int64_t m0 = (int64_t)mt * BMV;
   const int64_t n0 = (int64_t)blockIdx.y * BN;
-  if (TRI == TRI_LOWER && n0 > m0 + BM - 1) return;  // tile wholly above diagonal
+  if (TRI == TRI_LOWER && n0 > m0 + BMV - 1) return;  // tile wholly above diagonal
   if (TRI == TRI_UPPER && m0 > n0 + BN - 1) return;  // tile wholly below diagonal
   if (abort_flag != nullptr && *abort_flag != 0) return;  // a factorisation failed
 
   const bool all_nar = beta == PZ_NAR_BITS || (alpha == PZ_NAR_BITS && K > 0);
-  for (int i = tid; i < BM; i += NT) rowNaR[i] = 0;
+  for (int i = tid; i < BMV; i += NT) rowNaR[i] = 0;
   for (int j = tid; j < BN; j += NT) colNaR[j] = 0;
   for (int i = tid; i < 256; i += NT) {
     rtab[i] = pz_rtab_entry(i);
@@ -86,7 +89,7 @@ rgemm_kernel(int64_t M, int64_t N, int64_t K, uint32_t alpha,
 
   // Accumulators: padding elements (outside C or the triangle) start at 1
   // and are never stored; they only keep the warp on the fast path.
-  pz acc[TM][TN];
+  pz acc[TMV][TN];
   uint32_t c_nar = 0;  // bit i*TN+j: C_ij was NaR (beta != 0)
   // In-band fast path.  While every operand t = alpha op(B)_lj and op(A)_il
   // is zero or has its scale in [-40, 40], and every starting C value is zero
@@ -102,10 +105,10 @@ rgemm_kernel(int64_t M, int64_t N, int64_t K, uint32_t alpha,
   // operand outside the bounds.
   bool in_band = true;
 #pragma unroll
-  for (int i = 0; i < TM; ++i) {
+  for (int i = 0; i < TMV; ++i) {
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
-      int64_t r = m0 + tm * TM + i, c = n0 + tn * TN + j;
+      int64_t r = m0 + tm * TMV + i, c = n0 + tn * TN + j;
       pz v = pz_one();
       if (r < M && c < N && tri_ok<TRI>(r, c)) {
         if (beta == 0u) {
@@ -131,10 +134,10 @@ rgemm_kernel(int64_t M, int64_t N, int64_t K, uint32_t alpha,
     __syncthreads();  // previous tile fully consumed
     bool tile_ok = in_band;
 #pragma unroll
-    for (int q = 0; q < (BM * BK) / NT; ++q) {
+    for (int q = 0; q < (BMV * BK) / NT; ++q) {
       int e = tid + q * NT;
       int r, c;
-      if (!TA) { r = e % BM; c = e / BM; } else { c = e % BK; r = e / BK; }
+      if (!TA) { r = e % BMV; c = e / BMV; } else { c = e % BK; r = e / BK; }
       int64_t gr = m0 + r, gk = k0 + c;
       pz v = pz_one();
       if (gr < M && gk < K) {
@@ -176,13 +179,13 @@ rgemm_kernel(int64_t M, int64_t N, int64_t K, uint32_t alpha,
     if (in_band) {  // uniform over the CTA
 #pragma unroll 1
       for (int kk = 0; kk < kend; ++kk) {
-        pz a[TM], b[TN];
+        pz a[TMV], b[TN];
 #pragma unroll
-        for (int i = 0; i < TM; ++i) a[i] = As[kk][tm * TM + i];
+        for (int i = 0; i < TMV; ++i) a[i] = As[kk][tm * TMV + i];
 #pragma unroll
         for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tn * TN + j];
 #pragma unroll
-        for (int i = 0; i < TM; ++i) {
+        for (int i = 0; i < TMV; ++i) {
 #pragma unroll
           for (int j = 0; j < TN; ++j)
             acc[i][j] = pz_add_inband(rtab_in, acc[i][j], pz_mul_inband(rtab_in, b[j], a[i]));
@@ -191,13 +194,13 @@ rgemm_kernel(int64_t M, int64_t N, int64_t K, uint32_t alpha,
     } else {
 #pragma unroll 1
       for (int kk = 0; kk < kend; ++kk) {
-        pz a[TM], b[TN];
+        pz a[TMV], b[TN];
 #pragma unroll
-        for (int i = 0; i < TM; ++i) a[i] = As[kk][tm * TM + i];
+        for (int i = 0; i < TMV; ++i) a[i] = As[kk][tm * TMV + i];
 #pragma unroll
         for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tn * TN + j];
 #pragma unroll
-        for (int i = 0; i < TM; ++i) {
+        for (int i = 0; i < TMV; ++i) {
 #pragma unroll
           for (int j = 0; j < TN; ++j)
             acc[i][j] = pz_add_tab(rtab, acc[i][j], pz_mul_tab(rtab, b[j], a[i]));
@@ -207,12 +210,12 @@ rgemm_kernel(int64_t M, int64_t N, int64_t K, uint32_t alpha,
   }
 
 #pragma unroll
-  for (int i = 0; i < TM; ++i) {
+  for (int i = 0; i < TMV; ++i) {
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
-      int64_t r = m0 + tm * TM + i, c = n0 + tn * TN + j;
+      int64_t r = m0 + tm * TMV + i, c = n0 + tn * TN + j;
       if (r < M && c < N && tri_ok<TRI>(r, c)) {
-        int lr = tm * TM + i, lc = tn * TN + j;
+        int lr = tm * TMV + i, lc = tn * TN + j;
         bool nar = all_nar || ((c_nar >> (i * TN + j)) & 1u) ||
                    (kTot > 0 && (rowNaR[lr] | colNaR[lc]));
         C[r + c * ldc] = nar ? PZ_NAR_BITS : pz_to_bits(acc[i][j]);
@@ -222,25 +225,30 @@ rgemm_kernel(int64_t M, int64_t N, int64_t K, uint32_t alpha,
 }
 
 template <bool TA, bool TB, int TRI>
-int launch_one(dim3 grid, int64_t m, int64_t n, int64_t k, uint32_t alpha, const uint32_t *A,
-               int64_t lda, const uint32_t *B, int64_t ldb, uint32_t beta, uint32_t *C,
-               int64_t ldc, const int32_t *abort_flag, cudaStream_t stream) {
-  rgemm_kernel<TA, TB, TRI><<<grid, NT, 0, stream>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
-                                                      abort_flag);
+int launch_one(dim3 grid, bool narrow, int64_t m, int64_t n, int64_t k, uint32_t alpha,
+               const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb, uint32_t beta,
+               uint32_t *C, int64_t ldc, const int32_t *abort_flag, cudaStream_t stream) {
+  if (narrow)
+    rgemm_kernel<TA, TB, TRI, 2><<<grid, NT, 0, stream>>>(m, n, k, alpha, A, lda, B, ldb, beta, C,
+                                                           ldc, abort_flag);
+  else
+    rgemm_kernel<TA, TB, TRI, TM><<<grid, NT, 0, stream>>>(m, n, k, alpha, A, lda, B, ldb, beta, C,
+                                                            ldc, abort_flag);
   return launch_status();
 }
 
 template <int TRI>
-int launch_shape(bool ta, bool tb, dim3 grid, int64_t m, int64_t n, int64_t k, uint32_t alpha,
-                 const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb, uint32_t beta,
-                 uint32_t *C, int64_t ldc, const int32_t *abort_flag, cudaStream_t stream) {
+int launch_shape(bool ta, bool tb, dim3 grid, bool narrow, int64_t m, int64_t n, int64_t k,
+                 uint32_t alpha, const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb,
+                 uint32_t beta, uint32_t *C, int64_t ldc, const int32_t *abort_flag,
+                 cudaStream_t stream) {
   if (!ta && !tb)
-    return launch_one<false, false, TRI>(grid, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, abort_flag, stream);
+    return launch_one<false, false, TRI>(grid, narrow, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, abort_flag, stream);
   if (!ta && tb)
-    return launch_one<false, true, TRI>(grid, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, abort_flag, stream);
+    return launch_one<false, true, TRI>(grid, narrow, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, abort_flag, stream);
   if (ta && !tb)
-    return launch_one<true, false, TRI>(grid, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, abort_flag, stream);
-  return launch_one<true, true, TRI>(grid, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, abort_flag, stream);
+    return launch_one<true, false, TRI>(grid, narrow, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, abort_flag, stream);
+  return launch_one<true, true, TRI>(grid, narrow, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, abort_flag, stream);
 }
 
 template <int TRI>
@@ -248,7 +256,12 @@ int launch_tri(bool ta, bool tb, int64_t m, int64_t n, int64_t k, uint32_t alpha
                const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb,
                uint32_t beta, uint32_t *C, int64_t ldc, const int32_t *abort_flag,
                cudaStream_t stream) {
-  const int64_t gx = ceil_div(m, BM);
+  // Launches that would not fill one wave of 128 x 64 tiles (two CTAs on
+  // each of the 152 SMs; e.g. the rank-32 updates of tall, narrow panels)
+  // take 64 x 64 tiles instead: twice the CTAs for the same work.
+  const bool narrow = ceil_div(m, BM) * ceil_div(n, BN) < 2 * 152;
+  const int64_t bm = narrow ? BM / 2 : BM;
+  const int64_t gx = ceil_div(m, bm);
   if (gx > 0x7FFFFFFF) return POSIT_ERR_DEVICE;
   // gridDim.y is limited to 65535: split very wide C into column chunks
   const int64_t max_cols = (int64_t)65535 * BN;
@@ -263,8 +276,8 @@ int launch_tri(bool ta, bool tb, int64_t m, int64_t n, int64_t k, uint32_t alpha
     const dim3 grid = (TRI == TRI_FULL && gx > kGroupM && groups <= 65535)
                           ? dim3((unsigned)kGroupM, gy, (unsigned)groups)
                           : dim3((unsigned)gx, gy, 1);
-    int st = launch_shape<TRI>(ta, tb, grid, m, nc, k, alpha, A, lda, Bp, ldb, beta, Cp, ldc,
-                               abort_flag, stream);
+    int st = launch_shape<TRI>(ta, tb, grid, narrow, m, nc, k, alpha, A, lda, Bp, ldb, beta, Cp,
+                               ldc, abort_flag, stream);
     if (st != POSIT_OK) return st;
   }
   return POSIT_OK;

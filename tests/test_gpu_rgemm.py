@@ -58,6 +58,19 @@ def test_shapes_and_tails(m, n, k):
 
 
 @pytest.mark.parametrize("ta,tb", list(itertools.product("NT", "NT")))
+def test_wide_and_narrow_tiles_full(ta, tb):
+    """Launches that fill a wave of 128 x 64 tiles use them; smaller ones use
+    64 x 64 tiles.  Both, compared in full, with ragged edges and a C that
+    is read (beta = 1) and a NaR in op(A)."""
+    for m, n, k in ((2048 + 37, 1216 + 5, 33), (1000 + 7, 600 + 3, 29)):
+        A = words((m, k) if ta == "N" else (k, m), m + 11)
+        B = words((k, n) if tb == "N" else (n, k), m + 12)
+        C = words((m, n), m + 13)
+        A[(5, 3) if ta == "N" else (3, 5)] = 0x80000000
+        assert_same(run_gpu(ta, tb, MONE, A, B, ONE, C), oracle.rgemm(ta, tb, MONE, A, B, ONE, C))
+
+
+@pytest.mark.parametrize("ta,tb", list(itertools.product("NT", "NT")))
 @pytest.mark.parametrize("m", [2048, 2500, 4223])
 def test_grouped_launch_order_and_remainder(ta, tb, m):
     """More than 16 row tiles: complete groups of 16 row tiles in the grouped
