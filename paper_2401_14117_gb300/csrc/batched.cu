@@ -87,11 +87,11 @@ __device__ __forceinline__ pz sub_mul_inband(const pz_rtab *tab, pz x, pz a, pz 
 }
 
 // ---------------------------------------------------------------------------
-// Blocked factorisations inside one CTA.  Panels of BW columns (rows for the
-// upper Cholesky) are factored column by column; the rest of the matrix is
-// then brought up to date by a register-tiled update in which every element
-// receives the panel's BW terms in ascending order, exactly as the unblocked
-// algorithm orders them, so the result is the same for every panel width.
+// Blocked factorisations inside one CTA.  Panels of BW columns are factored
+// column by column; the rest of the matrix is then brought up to date by a
+// register-tiled update in which every element receives the panel's BW terms
+// in ascending order, exactly as the unblocked algorithm orders them, so the
+// result is the same for every panel width.
 // ---------------------------------------------------------------------------
 constexpr int BW = 16;             // panel width
 constexpr int TTM = 4, TTN = 2;    // register tile of the trailing update
@@ -337,79 +337,10 @@ __device__ int chol_decoded(pz *M, int n, pz *sh, const pz_rtab *tab, const pz_r
   return 0;
 }
 
-// Cholesky (upper, A = U^T U) of the decoded matrix, blocked by BW rows: the
-// transposed mirror of chol_decoded (row j is scaled, the trailing upper
-// triangle updated).  row: scratch of n elements for the scaled row.
-template <bool FAST>
-__device__ int chol_decoded_upper(pz *M, int n, pz *sh, const pz_rtab *tab, pz *row,
-                                  const pz_rtab *tab_in, bool ib) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-  bool oob = false;
-  for (int p0 = 0; p0 < n; p0 += BW) {
-    const int pe = min(n, p0 + BW);
-    for (int j = p0; j < pe; ++j) {
-      pz d = M[j + (size_t)j * n];
-      if (pz_is_nar(d) || pz_is_zero(d) || (d.m >> 31)) {
-        // the trailing triangle as the unblocked algorithm leaves it
-        if (pe < n)
-          trailing_update<FAST>(M, n, pe, n, pe, n, M + p0 + (size_t)pe * n, n, 1,
-                                M + p0 + (size_t)pe * n, 1, n, j - p0, 2, tab, tab_in, false);
-        return j + 1;
-      }
-      if (tid == 0) {
-        pz s = pz_sqrt(d);
-        sh[0] = s;
-        sh[1] = pz_div(pz_one(), s);
-      }
-      __syncthreads();
-      if (tid == 0) M[j + (size_t)j * n] = sh[0];
-      const pz r = sh[1];
-      for (int k = j + 1 + tid; k < n; k += nt) {
-        const pz a = M[j + (size_t)k * n];
-        const pz v = (FAST && ib) ? pz_mul_inband(tab_in, a, r) : mul_any<FAST>(tab, a, r);
-        M[j + (size_t)k * n] = v;
-        row[k] = v;  // row j of U, contiguous
-        oob |= out_of_band(v);
-      }
-      const bool any_oob = __syncthreads_or(oob);  // every thread reaches the barrier
-      const bool ib_update = FAST && ib && !any_oob;
-      oob = false;
-      // a_ik -= u_ji u_jk for the panel rows i in (j, pe), columns k >= i
-      for (int k = j + 1 + warp; k < n; k += nw) {
-        pz *col = M + (size_t)k * n;
-        const pz u = row[k];
-        const int ie = min(k + 1, pe);
-        if (ib_update) {
-          for (int i = j + 1 + lane; i < ie; i += 32) {
-            col[i] = sub_mul_inband(tab_in, col[i], row[i], u);
-            oob |= out_of_band(col[i]);
-          }
-        } else {
-          for (int i = j + 1 + lane; i < ie; i += 32) {
-            col[i] = sub_mul<FAST>(tab, col[i], row[i], u);
-            oob |= out_of_band(col[i]);
-          }
-        }
-      }
-      const bool upd_oob = __syncthreads_or(oob);  // every thread reaches the barrier
-      ib = ib && !upd_oob && !any_oob;
-      oob = false;
-    }
-    if (pe >= n) break;
-    // the trailing upper triangle: a_ik -= sum_t u_ti u_tk for i <= k
-    const pz *U12 = M + p0 + (size_t)pe * n;  // u(t, c) at U12[t + (c - pe) * n]
-    const bool ops_in = !block_out_of_band(U12, pe - p0, n - pe, 1, n);
-    const bool a22_oob = trailing_update<FAST>(M, n, pe, n, pe, n, U12, n, 1, U12, 1, n, pe - p0,
-                                               2, tab, tab_in, FAST && ib && ops_in);
-    ib = !a22_oob;
-  }
-  return 0;
-}
-
 // Rpotrs 'U' on the decoded factor: U^T y = b (updates from k ascending,
 // then / u_ii), U x = y (updates from k descending, then / u_ii); both run
-// column by column with the rows in parallel.
+// column by column with the rows in parallel.  The factor is held transposed:
+// u_ik = M[k + i * n] (the lower triangle of M is U^T).
 __device__ void potrs_decoded_upper(const pz *M, int n, pz *X, int nrhs) {
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int k = 0; k < n; ++k) {
@@ -418,7 +349,7 @@ __device__ void potrs_decoded_upper(const pz *M, int n, pz *X, int nrhs) {
     const int m = n - k - 1;
     for (int idx = tid; idx < m * nrhs; idx += nt) {
       int i = k + 1 + idx % m, c = idx / m;
-      X[i + c * n] = pz_sub(X[i + c * n], pz_mul(M[k + (size_t)i * n], X[k + c * n]));
+      X[i + c * n] = pz_sub(X[i + c * n], pz_mul(M[i + (size_t)k * n], X[k + c * n]));
     }
     __syncthreads();
   }
@@ -427,7 +358,7 @@ __device__ void potrs_decoded_upper(const pz *M, int n, pz *X, int nrhs) {
     __syncthreads();
     for (int idx = tid; idx < k * nrhs; idx += nt) {
       int i = idx % k, c = idx / k;
-      X[i + c * n] = pz_sub(X[i + c * n], pz_mul(M[i + (size_t)k * n], X[k + c * n]));
+      X[i + c * n] = pz_sub(X[i + c * n], pz_mul(M[k + (size_t)i * n], X[k + c * n]));
     }
     __syncthreads();
   }
@@ -531,8 +462,8 @@ __global__ void __launch_bounds__(512) batched_kernel(const posit_problem *__res
     if (qi < 0) break;
     const posit_problem P = probs[order ? order[qi] : qi];
     const int n = P.n, nrhs = P.nrhs;
-    // M (n x n), X (n x nrhs), then scratch of n * max(nrhs, 1): the products
-    // of the dot-form solve, or row j of U in the upper Cholesky
+    // M (n x n), X (n x nrhs), then scratch of n * max(nrhs, 1) (the products
+    // of the dot-form solve)
     const size_t need = (size_t)n * n + (size_t)n * nrhs + (size_t)n * (nrhs > 1 ? nrhs : 1);
     pz *M = need <= (size_t)smem_elems ? sm : ws;
     pz *X = M + (size_t)n * n;
@@ -541,10 +472,14 @@ __global__ void __launch_bounds__(512) batched_kernel(const posit_problem *__res
     if (tid == 0) s_nar = 0;
     __syncthreads();
     int nar = 0, oob = 0;
+    // the upper Cholesky is factored as the lower one of the transposed
+    // upper triangle (the same operations on mirrored indices): M(i, k) =
+    // a(k, i) for i >= k
     for (int idx = tid; idx < n * n; idx += nt) {
       int i = idx % n, k = idx / n;
-      bool skip = (lower_only && k > i) || (upper_only && k < i);
-      const uint32_t w = skip ? 0u : P.A[i + (int64_t)k * P.lda];
+      bool skip = (lower_only || upper_only) && k > i;
+      const uint32_t w =
+          skip ? 0u : (upper_only ? P.A[k + (int64_t)i * P.lda] : P.A[i + (int64_t)k * P.lda]);
       nar |= w == PZ_NAR_BITS;
       const pz v = pz_decode(w);
       oob |= out_of_band(v);
@@ -568,15 +503,18 @@ __global__ void __launch_bounds__(512) batched_kernel(const posit_problem *__res
                   : chol_decoded<false>(M, n, sh, rtab, rtab_in, false);
       if (info == 0) potrs_decoded(M, n, X, nrhs, prod);
     } else {
-      info = fast ? chol_decoded_upper<true>(M, n, sh, rtab, prod, rtab_in, ib0)
-                  : chol_decoded_upper<false>(M, n, sh, rtab, prod, rtab_in, false);
+      info = fast ? chol_decoded<true>(M, n, sh, rtab, rtab_in, ib0)
+                  : chol_decoded<false>(M, n, sh, rtab, rtab_in, false);
       if (info == 0) potrs_decoded_upper(M, n, X, nrhs);
     }
     __syncthreads();
     for (int idx = tid; idx < n * n; idx += nt) {
       int i = idx % n, k = idx / n;
-      if ((lower_only && k > i) || (upper_only && k < i)) continue;
-      P.A[i + (int64_t)k * P.lda] = pz_to_bits(M[idx]);
+      if ((lower_only || upper_only) && k > i) continue;
+      if (upper_only)
+        P.A[k + (int64_t)i * P.lda] = pz_to_bits(M[idx]);
+      else
+        P.A[i + (int64_t)k * P.lda] = pz_to_bits(M[idx]);
     }
     if (P.kind == POSIT_LU || info == 0)
       for (int idx = tid; idx < n * nrhs; idx += nt) {
