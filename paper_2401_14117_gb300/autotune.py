@@ -14,7 +14,10 @@ import os
 
 SMEM_PER_SM = 228 * 1024          # GB300 shared memory per SM
 SMEM_PER_CTA_MAX = 227 * 1024
-THREADS_PER_SM = 512   # the batched kernel holds 128 registers per thread
+# threads per SM a plan may ask for; the batched kernel holds 128 registers per
+# thread, so at most 512 of them are resident at once and CTAs beyond that
+# wait (plans asking for more are still valid and sometimes faster)
+THREADS_PER_SM = 1024
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE_PATH = os.path.join(_HERE, "_build", "autotune_cache.json")

@@ -62,7 +62,7 @@ class Pool:
 
 
 def default_config(budget_gb=40.0, small_n_max=512, max_batch=1024, max_nrhs=8,
-                   plan=(512, 1, 96 * 1024), large_lanes=16):
+                   plan=(256, 4, 48 * 1024), large_lanes=16):
     return binding.posit_serve_config(int(budget_gb * 2 ** 30), small_n_max, max_batch,
                                       max_nrhs, large_lanes, binding.posit_plan(*plan, 0))
 
