@@ -44,11 +44,12 @@ ONE = 0x40000000
 # inner loop, so they scale with M N K): integer-ALU-pipe warp instructions
 # (sm__inst_executed_pipe_alu.sum / M N K) and all warp instructions
 # (smsp__inst_executed.sum / M N K).
-ALU_INST_PER_MAC = 1.5015  # 8.25440e11 / 5.49756e11 (NN 8192^3)
-INST_PER_MAC = 2.0018      # 1.10052e12 / 5.49756e11
+ALU_INST_PER_MAC = 1.2211  # 6.71285e11 / 5.49756e11 (NN 8192^3)
+INST_PER_MAC = 1.9421      # 1.06769e12 / 5.49756e11
+FMA_INST_PER_MAC = 0.5862  # sm__inst_executed_pipe_fmaheavy.sum: 3.22281e11 / 5.49756e11
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one captured
 # 8192^3 launch.
-TRAFFIC_8192 = 4.96e9 + 0.42048e9
+TRAFFIC_8192 = 5.01174e9 + 0.42110e9
 # The kernel is bound by the integer ALU pipe: 16 lanes per scheduler, i.e.
 # 0.5 warp instruction per clock per scheduler (the rate at which ncu's
 # sm__inst_executed_pipe_alu.avg.pct_of_peak_sustained_active reads 100 %).
@@ -353,8 +354,9 @@ def run_ours(args):
                 "unit": "G ALU-pipe warp-inst/s", "frac": achieved / peak,
                 "traffic": traffic, "traffic_unit": "bytes per launch",
                 "algorithmic_bytes": 4.0 * (m * k + k * n + m * n),
-                "kernel": "rgemm_kernel<false,false,0>", "launch_ms": launch_ms,
+                "kernel": "rgemm_kernel<false,false,0,4>", "launch_ms": launch_ms,
                 "alu_inst_per_mac": ALU_INST_PER_MAC, "inst_per_mac": INST_PER_MAC,
+                "fma_inst_per_mac": FMA_INST_PER_MAC,
                 "peak_basis": (f"{SM_COUNT} SMs x {SCHEDULERS_PER_SM} schedulers x "
                                f"{ALU_WARP_INST_PER_CLK} ALU-pipe warp-inst/clk x {peak_clock:.0f} MHz"),
                 "issue": {"achieved": issue, "peak": issue_peak, "frac": issue / issue_peak,

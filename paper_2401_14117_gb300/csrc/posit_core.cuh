@@ -128,29 +128,41 @@ static __device__ __forceinline__ pz pz_round(uint32_t sign, int S, uint32_t X) 
   return pz{S + (int)c, sign | (r >> c)};
 }
 
+// 32-bit a * b + c on the integer multiply-add pipe.  Written as PTX so that
+// the compiler keeps the multiply (by a value it cannot see, such as a power
+// of two read from a table) instead of turning it back into shifts and adds
+// on the ALU pipe, which is the one the multiply-add loops are bound by.
+static __device__ __forceinline__ uint32_t pz_imad(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+
 // Rounding constants per scale, for kernels that keep a 256-entry table in
 // shared memory (index S + 128).  q = 2 + m bits are dropped below the kept
-// ones (lead at bit 30); scales whose regime has 28 or more bits, and every
-// scale outside [-128, 127] (zero, saturation), are marked q = 255 and take
+// ones (lead at bit 30).  Scales whose regime has 28 or more bits, and every
+// scale outside [-128, 127] (zero, saturation), are marked tie = 0 and take
 // the general path.
 struct __align__(16) pz_rtab {
-  uint32_t keep;  // ~((1 << q) - 1)
-  uint32_t hm1;   // (1 << (q - 1)) - 1
-  uint32_t q;
-  uint32_t pad;
+  uint32_t keep;   // ~((1 << q) - 1)
+  uint32_t hm1;    // (1 << (q - 1)) - 1
+  uint32_t tie;    // 1 << (31 - q): X * tie has bit q of X (the tie-breaking lsb) at bit 31
+  uint32_t carry;  // 0xC0000000: added to the result word when the rounding carries out
 };
+
+static __device__ __forceinline__ pz_rtab pz_rtab_make(uint32_t q) {
+  pz_rtab e;
+  e.keep = 0xFFFFFFFFu << q;
+  e.hm1 = (1u << (q - 1)) - 1u;
+  e.tie = 1u << (31 - q);
+  e.carry = 0xC0000000u;
+  return e;
+}
 
 static __device__ __forceinline__ pz_rtab pz_rtab_entry(int i) {
   int S = i - 128, k = S >> 2, m = k >= 0 ? k + 1 : -k;
-  pz_rtab e;
-  if (m >= 28) {
-    e.keep = 0; e.hm1 = 0; e.q = 255u;
-  } else {
-    uint32_t q = 2u + (uint32_t)m;
-    e.keep = 0xFFFFFFFFu << q; e.hm1 = (1u << (q - 1)) - 1u; e.q = q;
-  }
-  e.pad = 0;
-  return e;
+  if (m >= 28) return pz_rtab{0u, 0u, 0u, 0xC0000000u};
+  return pz_rtab_make(2u + (uint32_t)m);
 }
 
 // Table for values known to stay inside the fast band (see pz_round_inband),
@@ -159,10 +171,23 @@ static __device__ __forceinline__ pz_rtab pz_rtab_entry(int i) {
 // zero (significand 0) may land on any row: every row rounds 0 to 0.
 static __device__ __forceinline__ pz_rtab pz_rtab_inband_entry(int i) {
   pz_rtab e = pz_rtab_entry(((i ^ 128) - 128) + 128);
-  if (e.q > 31u) {
-    e.keep = 0xC0000000u; e.hm1 = (1u << 29) - 1u; e.q = 30u;
-  }
+  if (e.tie == 0u) e = pz_rtab_make(30u);
   return e;
+}
+
+// Round to nearest, ties to even, of sign * 2^S * X / 2^30 with the constants
+// of the scale S.  The tie-breaking lsb (bit q of X) comes from a multiply;
+// rf = X + hm1 + lsb reaches bit 31 only when the kept bits were all ones and
+// round up to 2^31 (then r = 2^31 exactly, carry c = 1, scale S + 1, 2^30).
+// The sign is put in with the mask, and the carry case is fixed by adding
+// c * 0xC0000000 (mod 2^32): (2^31 ^ sign) + 0xC0000000 = sign | 2^30.
+static __device__ __forceinline__ pz pz_round_apply(const pz_rtab &e, uint32_t sign, int S,
+                                                    uint32_t X) {
+  const uint32_t lsb = pz_imad(X, e.tie, 0u) >> 31;
+  const uint32_t rf = X + e.hm1 + lsb;
+  const uint32_t rs = (rf & e.keep) ^ sign;
+  const uint32_t c = rf >> 31;
+  return pz{S + (int)c, pz_imad(c, e.carry, rs)};
 }
 
 // pz_round_tab without the test for the regimes of 28 or more bits: only for
@@ -170,22 +195,15 @@ static __device__ __forceinline__ pz_rtab pz_rtab_inband_entry(int i) {
 // the table of pz_rtab_inband_entry.
 static __device__ __forceinline__ pz pz_round_inband(const pz_rtab *tab, uint32_t sign, int S,
                                                      uint32_t X) {
-  const pz_rtab e = tab[S & 255];
-  uint32_t lsb = (X >> e.q) & 1u;
-  uint32_t r = (X + e.hm1 + lsb) & e.keep;
-  uint32_t c = r >> 31;
-  return pz{S + (int)c, sign | (r >> c)};
+  return pz_round_apply(tab[S & 255], sign, S, X);
 }
 
 // pz_round with the per-scale constants read from the table.
 static __device__ __forceinline__ pz pz_round_tab(const pz_rtab *tab, uint32_t sign, int S,
                                                   uint32_t X) {
   const pz_rtab e = tab[min((unsigned)(S + 128), 255u)];
-  if (e.q > 31u) return pz_round(sign, S, X);
-  uint32_t lsb = (X >> e.q) & 1u;
-  uint32_t r = (X + e.hm1 + lsb) & e.keep;
-  uint32_t c = r >> 31;
-  return pz{S + (int)c, sign | (r >> c)};
+  if (e.tie == 0u) return pz_round(sign, S, X);
+  return pz_round_apply(e, sign, S, X);
 }
 
 // ---------------------------------------------------------------------------
@@ -209,9 +227,10 @@ static __device__ __forceinline__ void pz_mul_exact(pz a, pz b, uint32_t &sign, 
   uint64_t P = (uint64_t)A * (uint64_t)B;
   uint32_t hi = (uint32_t)(P >> 32), lo = (uint32_t)P;
   uint32_t t = hi >> 30;           // 1 if the leading one is at bit 62
-  // leading one to bit 30; every bit of lo below is jammed into bit 0 (bit 0
-  // is below the guard bit, so the lo bit shifted in needs no special care)
-  X = __funnelshift_l(lo, hi, 1u - t) | min(lo, 1u);
+  // leading one to bit 30: hi, or 2 hi = hi * (t ^ 1) + hi (a multiply-add);
+  // every bit of lo is jammed into bit 0 (below the guard bit, so the lo bit
+  // that a shift by one would bring in needs no special care)
+  X = pz_imad(hi, t ^ 1u, hi) | min(lo, 1u);
   S = a.s + b.s + (int)t;
   sign = (a.m ^ b.m) & 0x80000000u;
 }

@@ -13,9 +13,11 @@
 //     whole k loop, and applies c = c + t * a for l ascending -- TM*TN
 //     independent dependency chains per thread, and two 16-warp CTAs per SM,
 //     hide the integer pipeline latency;
-//   * the scale-dependent rounding constants (bits to drop, half-ulp mask)
-//     come from a 256-entry table in shared memory instead of being derived
-//     from the scale on the ALU pipe for every operation;
+//   * the scale-dependent rounding constants (half-ulp mask, kept-bits mask,
+//     a power of two that brings the tie-breaking bit to bit 31, and the
+//     carry fix-up constant) come from a 256-entry table in shared memory, so
+//     that the tie bit and the carry are multiply-adds: the integer ALU pipe,
+//     which bounds the kernel, is left the shifts, masks and selects;
 //   * C is encoded to posit words once, at the end.
 // The per-element order is exactly the reference-BLAS order, so the result
 // does not depend on BM/BN/BK or the grid.
