@@ -44,12 +44,12 @@ ONE = 0x40000000
 # inner loop, so they scale with M N K): integer-ALU-pipe warp instructions
 # (sm__inst_executed_pipe_alu.sum / M N K) and all warp instructions
 # (smsp__inst_executed.sum / M N K).
-ALU_INST_PER_MAC = 1.2211  # 6.71285e11 / 5.49756e11 (NN 8192^3)
-INST_PER_MAC = 1.9421      # 1.06769e12 / 5.49756e11
-FMA_INST_PER_MAC = 0.5862  # sm__inst_executed_pipe_fmaheavy.sum: 3.22281e11 / 5.49756e11
+ALU_INST_PER_MAC = 1.1273  # 6.19745e11 / 5.49756e11 (NN 8192^3)
+INST_PER_MAC = 2.0086      # 1.10426e12 / 5.49756e11
+FMA_INST_PER_MAC = 0.7464  # sm__inst_executed_pipe_fmaheavy.sum: 4.10328e11 / 5.49756e11
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one captured
 # 8192^3 launch.
-TRAFFIC_8192 = 5.01174e9 + 0.42110e9
+TRAFFIC_8192 = 4.98842e9 + 0.42116e9
 # The kernel is bound by the integer ALU pipe: 16 lanes per scheduler, i.e.
 # 0.5 warp instruction per clock per scheduler (the rate at which ncu's
 # sm__inst_executed_pipe_alu.avg.pct_of_peak_sustained_active reads 100 %).

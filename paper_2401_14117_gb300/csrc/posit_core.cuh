@@ -297,21 +297,50 @@ static __device__ __forceinline__ pz pz_add_fast(pz c, pz t) {
   return pz_round(sign, S, X);
 }
 
+// Shift that brings the leading one of x to bit 31 (the count of leading
+// zeros) for x != 0, and 0xFFFFFFFF for x = 0: one bfind instruction, without
+// the fix-up that makes a count of leading zeros return 32 for 0.
+static __device__ __forceinline__ uint32_t pz_lead_shift(uint32_t x) {
+  uint32_t d;
+  asm("bfind.shiftamt.u32 %0, %1;" : "=r"(d) : "r"(x));
+  return d;
+}
+
 // pz_add_exact for the in-band path: clamping funnel shifts instead of
 // capping the alignment at 31 (a shift of 32 or more moves every bit into the
 // jam), normalisation through the form with the leading one at bit 31, and a
-// zero sum (count of leading zeros 32) placed 2^20 below the larger operand's
-// scale by a multiply-add instead of a select.  Same values as pz_add_exact
-// for the in-band operands; a zero keeps a significand of 0 and a scale far
-// below every nonzero in-band scale.
-static __device__ __forceinline__ void pz_add_exact_inband(pz c, pz t, uint32_t &sign, int &Sout,
-                                                           uint32_t &Xout) {
-  bool sw = t.s > c.s;
-  int SL = sw ? t.s : c.s;
-  int SS = sw ? c.s : t.s;
-  uint32_t mL = sw ? t.m : c.m;
-  uint32_t mS = sw ? c.m : t.m;
-  uint32_t d = (uint32_t)(SL - SS);
+// zero sum (normalisation shift 0xFFFFFFFF) placed about 2^20 below the
+// larger operand's scale by a multiply-add instead of a select.  Same values
+// as pz_add_exact for the in-band operands; a zero keeps a significand of 0
+// and a scale far below every nonzero in-band scale.
+//
+// BLEND picks the larger-scale operand with multiply-adds instead of selects:
+// with w = 1 when t has the larger scale (else 0), mL = c.m + w (t.m - c.m)
+// and mS = t.m + w (c.m - t.m), where neg1 = 0xFFFFFFFF comes from the
+// caller as a value the compiler cannot see (a kernel argument), so that the
+// differences stay multiply-adds on the FMA pipe and the ALU pipe, which
+// bounds the multiply-add loops, is spared the selects.
+template <bool BLEND>
+static __device__ __forceinline__ void pz_add_exact_inband_t(pz c, pz t, uint32_t neg1,
+                                                             uint32_t &sign, int &Sout,
+                                                             uint32_t &Xout) {
+  int SL;
+  uint32_t d, mL, mS;
+  if (BLEND) {
+    const int dd = c.s - t.s;
+    const uint32_t w = (uint32_t)dd >> 31;  // t.s > c.s
+    SL = max(c.s, t.s);
+    d = (uint32_t)abs(dd);
+    mL = pz_imad(w, pz_imad(c.m, neg1, t.m), c.m);
+    mS = pz_imad(w, pz_imad(t.m, neg1, c.m), t.m);
+  } else {
+    const bool sw = t.s > c.s;
+    SL = sw ? t.s : c.s;
+    const int SS = sw ? c.s : t.s;
+    mL = sw ? t.m : c.m;
+    mS = sw ? c.m : t.m;
+    d = (uint32_t)(SL - SS);
+  }
   uint32_t magL = mL & 0x7FFFFFFFu;
   uint32_t magS = mS & 0x7FFFFFFFu;
   uint32_t shv = __funnelshift_rc(magS, 0u, d);   // magS >> d, 0 from 32 on
@@ -322,18 +351,32 @@ static __device__ __forceinline__ void pz_add_exact_inband(pz c, pz t, uint32_t 
   uint32_t neg = sub & (R >> 31);  // difference went negative (d = 0 only)
   R = neg ? (0u - R) : R;
   sign = (mL & 0x80000000u) ^ (neg << 31);
-  const int lz = __clz(R);
+  const uint32_t lz = pz_lead_shift(R);
   // lead at bit 31 (R << lz; 0 for R = 0), then back to bit 30 with the bit
   // shifted out jammed (it can only be nonzero when lz = 0)
-  const uint32_t Y = __funnelshift_lc(0u, R, (uint32_t)lz);
+  const uint32_t Y = __funnelshift_lc(0u, R, lz);
   Xout = (Y >> 1) | (Y & 1u);
-  Sout = (SL + 1 - lz) + (lz & 32) * -32768;
+  Sout = (SL + 1 - (int)lz) + (int)(lz & 32u) * -32768;
+}
+
+static __device__ __forceinline__ void pz_add_exact_inband(pz c, pz t, uint32_t &sign, int &Sout,
+                                                           uint32_t &Xout) {
+  pz_add_exact_inband_t<false>(c, t, 0u, sign, Sout, Xout);
 }
 
 static __device__ __forceinline__ pz pz_add_inband(const pz_rtab *tab, pz c, pz t) {
   uint32_t sign, X;
   int S;
   pz_add_exact_inband(c, t, sign, S, X);
+  return pz_round_inband(tab, sign, S, X);
+}
+
+// pz_add_inband with the operand pick by multiply-adds (neg1 = 0xFFFFFFFF).
+static __device__ __forceinline__ pz pz_add_inband_blend(const pz_rtab *tab, uint32_t neg1, pz c,
+                                                         pz t) {
+  uint32_t sign, X;
+  int S;
+  pz_add_exact_inband_t<true>(c, t, neg1, sign, S, X);
   return pz_round_inband(tab, sign, S, X);
 }
 

@@ -52,7 +52,10 @@ __global__ void __launch_bounds__(NT, 2)
 rgemm_kernel(int64_t M, int64_t N, int64_t K, uint32_t alpha,
              const uint32_t *__restrict__ A, int64_t lda,
              const uint32_t *__restrict__ B, int64_t ldb, uint32_t beta,
-             uint32_t *__restrict__ C, int64_t ldc, const int32_t *__restrict__ abort_flag) {
+             uint32_t *__restrict__ C, int64_t ldc, const int32_t *__restrict__ abort_flag,
+             uint32_t neg1) {
+  // neg1 = 0xFFFFFFFF: the multiplier of the in-band addition's operand pick
+  // (pz_add_inband_blend), an argument so that it stays a multiply-add
   constexpr int BMV = 32 * TMV;  // CTA rows: 32 row groups of TMV rows
   constexpr int GMV = BMV / TMV;
   static_assert(GMV * (BN / TN) == NT, "thread tile");
@@ -190,7 +193,8 @@ rgemm_kernel(int64_t M, int64_t N, int64_t K, uint32_t alpha,
         for (int i = 0; i < TMV; ++i) {
 #pragma unroll
           for (int j = 0; j < TN; ++j)
-            acc[i][j] = pz_add_inband(rtab_in, acc[i][j], pz_mul_inband(rtab_in, b[j], a[i]));
+            acc[i][j] = pz_add_inband_blend(rtab_in, neg1, acc[i][j],
+                                            pz_mul_inband(rtab_in, b[j], a[i]));
         }
       }
     } else {
@@ -232,10 +236,10 @@ int launch_one(dim3 grid, bool narrow, int64_t m, int64_t n, int64_t k, uint32_t
                uint32_t *C, int64_t ldc, const int32_t *abort_flag, cudaStream_t stream) {
   if (narrow)
     rgemm_kernel<TA, TB, TRI, 2><<<grid, NT, 0, stream>>>(m, n, k, alpha, A, lda, B, ldb, beta, C,
-                                                           ldc, abort_flag);
+                                                           ldc, abort_flag, 0xFFFFFFFFu);
   else
     rgemm_kernel<TA, TB, TRI, TM><<<grid, NT, 0, stream>>>(m, n, k, alpha, A, lda, B, ldb, beta, C,
-                                                            ldc, abort_flag);
+                                                            ldc, abort_flag, 0xFFFFFFFFu);
   return launch_status();
 }
 
