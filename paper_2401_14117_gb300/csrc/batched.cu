@@ -408,7 +408,7 @@ __device__ void potrs_decoded(const pz *M, int n, pz *X, int nrhs, pz *prod) {
     __syncthreads();
   }
   // x_i = (y_i - sum_{k>i, ascending} l_ki x_k) / l_ii: products in parallel
-  // (stored negated), one serial chain of fast additions per right-hand side;
+  // (stored negated), one serial chain of short-path additions per right-hand side;
   // a NaR product or y_i makes x_i NaR
   for (int i = n - 1; i >= 0; --i) {
     const int m = n - i - 1;
@@ -421,10 +421,13 @@ __device__ void potrs_decoded(const pz *M, int n, pz *X, int nrhs, pz *prod) {
     for (int c = tid; c < nrhs; c += nt) {
       pz acc = X[i + c * n];
       bool nar = pz_is_nar(acc);
+      const pz *pr = prod + c * m;
+      pz pn = pr[0];
       for (int t = 0; t < m; ++t) {
-        pz p = prod[t + c * m];
+        const pz p = pn;
+        pn = pr[t + 1];  // loaded ahead; prod holds n * max(nrhs, 1) > m * nrhs entries
         nar |= p.s >= PZ_NAR_T;
-        acc = pz_add_fast(acc, p);
+        acc = pz_add_serial(acc, p);
       }
       acc = nar ? pz_nar() : pz_canon(acc, false);
       X[i + c * n] = pz_div(acc, M[i + (size_t)i * n]);

@@ -387,6 +387,59 @@ static __device__ __forceinline__ pz pz_add_tab(const pz_rtab *tab, pz c, pz t) 
   return pz_round_tab(tab, sign, S, X);
 }
 
+// c (+) t with a short dependency path, for the serial chains of the
+// dot-form solves (one rounded addition per link, each waiting for the last).
+// Same result as pz_add_fast for every pair of non-NaR operands.  Both
+// alignment directions are formed at once, so the choice of the larger operand
+// is a select after the shifts instead of before them; the three normalisations
+// a sum can need when it loses at most one bit -- a carry into bit 31, none, or
+// one bit of cancellation -- are formed side by side from the sum, each with
+// the rounding constants of its scale (SL + 1, SL, SL - 1, computed from the
+// larger scale SL while the sum is formed), and the sum's magnitude picks
+// one.  The rare cases go to pz_add_fast: a difference that went negative or
+// cancelled more than one bit (zero included), and a larger scale outside
+// [-107, 106], whose neighbours may have a regime of 28 or more bits (zero and
+// NaR operands have scales far outside).
+struct pz_rq {
+  uint32_t hm1, keep, q;
+};
+
+// Rounding constants of a scale whose regime is shorter than 28 bits.
+static __device__ __forceinline__ pz_rq pz_rq_of(int S) {
+  const uint32_t q = (uint32_t)((S >> 2) ^ (S >> 31)) + 3u;  // 2 + regime run length
+  return pz_rq{(1u << (q - 1)) - 1u, 0xFFFFFFFFu << q, q};
+}
+
+static __device__ __forceinline__ pz pz_add_serial(pz c, pz t) {
+  const uint32_t magC = c.m & 0x7FFFFFFFu, magT = t.m & 0x7FFFFFFFu;
+  const int dd = c.s - t.s, nd = t.s - c.s;  // a negative count clamps to 32
+  const int SL = max(c.s, t.s);
+  const bool sw = nd > 0;  // t has the larger scale
+  const bool sub = (int)(c.m ^ t.m) < 0;
+  const uint32_t shT = __funnelshift_rc(magT, 0u, (uint32_t)dd) |
+                       min(__funnelshift_rc(0u, magT, (uint32_t)dd), 1u);
+  const uint32_t shC = __funnelshift_rc(magC, 0u, (uint32_t)nd) |
+                       min(__funnelshift_rc(0u, magC, (uint32_t)nd), 1u);
+  const uint32_t magL = sw ? magT : magC;
+  const uint32_t sS = sw ? shC : shT;
+  const uint32_t sign = (sw ? t.m : c.m) & 0x80000000u;
+  const uint32_t Rs = magL - sS;
+  const uint32_t R = sub ? Rs : magL + sS;
+  const pz_rq kA = pz_rq_of(SL + 1), kB = pz_rq_of(SL), kC = pz_rq_of(SL - 1);
+  const bool c0 = R >= 0x80000000u, c1 = R >= 0x40000000u;  // carry / no shift / one bit
+  const uint32_t X = c0 ? ((R >> 1) | (R & 1u)) : (c1 ? R : R << 1);
+  const uint32_t lsb = c0 ? (R >> (kA.q + 1u)) & 1u : (c1 ? (R >> kB.q) & 1u : (R >> (kC.q - 1u)) & 1u);
+  const uint32_t hm1 = c0 ? kA.hm1 : (c1 ? kB.hm1 : kC.hm1);
+  const uint32_t keep = c0 ? kA.keep : (c1 ? kB.keep : kC.keep);
+  const int S = c0 ? SL + 1 : (c1 ? SL : SL - 1);
+  const uint32_t r = (X + hm1 + lsb) & keep;
+  const uint32_t cy = r >> 31;
+  pz res{S + (int)cy, sign | (r >> cy)};
+  const bool slow = (sub && (int)Rs < 0) || R < 0x20000000u || (unsigned)(SL + 107) > 213u;
+  if (slow) res = pz_add_fast(c, t);
+  return res;
+}
+
 // General a (x) b and c (+) t: NaR in, NaR out, and the zero / NaR scales
 // are put back to their canonical values so that chains of operations never
 // drift between the two ranges.

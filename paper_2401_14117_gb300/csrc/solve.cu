@@ -192,13 +192,13 @@ __global__ void __launch_bounds__(ST, 1) trsv_wave_kernel(TriArgs a) {
 // A[k + i*lda] (column i below the diagonal).  The products of a row are
 // formed in parallel (the next chunk while the current one is consumed) and
 // stored negated; one thread runs the chain of rounded additions, the only
-// serial part, with the NaR-free fast add (a NaR product or b_i makes x_i
-// NaR; that test is off the chain's dependency path).
+// serial part, with the short-path addition pz_add_serial (a NaR product or
+// b_i makes x_i NaR; that test is off the chain's dependency path).
 __global__ void __launch_bounds__(ST) trsv_dot_backward_kernel(const uint32_t *__restrict__ A,
                                                                 int64_t lda, uint32_t *B,
                                                                 int64_t ldb, int64_t n, int unit,
                                                                 const int32_t *abort_flag) {
-  __shared__ pz prod[2][ST];
+  __shared__ pz prod[2][ST + 1];
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pz *x = reinterpret_cast<pz *>(smem_raw);  // [n] the right-hand side / solution
   uint32_t *b = B + (int64_t)blockIdx.x * ldb;
@@ -228,10 +228,12 @@ __global__ void __launch_bounds__(ST) trsv_dot_backward_kernel(const uint32_t *_
       if (tid == 0) {
         const int cnt = (int)min64(ST, n - k0);
         const pz *pr = prod[buf];
+        pz pn = pr[0];
         for (int t = 0; t < cnt; ++t) {
-          pz p = pr[t];
+          const pz p = pn;
+          pn = pr[t + 1];  // next link's product, loaded ahead (row padded by one)
           nar |= p.s >= PZ_NAR_T;
-          acc = pz_add_fast(acc, p);
+          acc = pz_add_serial(acc, p);
         }
       }
       __syncthreads();
