@@ -14,7 +14,7 @@ import torch
 
 import oracle
 from paper_2401_14117_gb300 import binding, inputs
-from tests.gpu_util import DEV, from_dev, to_dev
+from tests.gpu_util import DEV, from_dev, mixed_words, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -240,6 +240,61 @@ def test_potrs_matches_oracle(uplo, n, nrhs):
     binding.posit_rpotrs(uplo, n, nrhs, dF, n, dB, n)
     torch.cuda.synchronize()
     assert_same(from_dev(dB), want, "potrs")
+
+
+def _chain_factor(case, n, rng):
+    """A factor whose dot-form backward solve (L^T x = y) runs its serial chain
+    through every path of the chain addition: 'range' -- random words of any
+    scale (long regimes, saturation), 'cancel' -- entries +-2^j with small
+    right-hand sides, so that sums cancel one or many bits or vanish, 'edges'
+    -- magnitudes near 2^+-106, where the result scale meets the long-regime
+    band.  Zeros are sprinkled in; U (for Rgetrs) is the identity."""
+    if case == "range":
+        F = mixed_words(rng, n * n).reshape(n, n)
+        F[F == 0x80000000] = ONE
+    elif case == "cancel":
+        v = np.ldexp(rng.choice([-1.0, 1.0], size=(n, n)), rng.integers(-3, 1, size=(n, n)))
+        F = oracle.from_double_array(v)
+    else:
+        e = rng.choice([-1, 1], size=(n, n)) * rng.integers(100, 111, size=(n, n))
+        v = np.ldexp(rng.uniform(1.0, 2.0, size=(n, n)) * rng.choice([-1.0, 1.0], size=(n, n)),
+                     e // 2)
+        F = oracle.from_double_array(v)
+    F[rng.random((n, n)) < 0.05] = 0
+    d = np.abs(oracle.to_double_array(np.diag(F)))
+    np.fill_diagonal(F, oracle.from_double_array(np.where(d > 0, d, 1.0)))
+    return F
+
+
+@pytest.mark.parametrize("case", ["range", "cancel", "edges"])
+@pytest.mark.parametrize("kind", ["getrs_T", "potrs_L"])
+def test_dot_form_chain_paths(case, kind):
+    n, nrhs = 300, 3
+    rng = np.random.default_rng(77 + len(case))
+    F = _chain_factor(case, n, rng)
+    if case == "range":
+        B = mixed_words(rng, n * nrhs).reshape(n, nrhs)
+        B[B == 0x80000000] = 0
+    elif case == "cancel":
+        B = oracle.from_double_array(rng.uniform(-0.01, 0.01, size=(n, nrhs)))
+    else:
+        B = oracle.from_double_array(np.ldexp(rng.uniform(-2, 2, size=(n, nrhs)), 106))
+    B[rng.random((n, nrhs)) < 0.05] = 0
+    B[n // 2, 2] = 0x80000000  # a NaR right-hand side entry
+    dF, dB = to_dev(F), to_dev(B)
+    if kind == "getrs_T":
+        Fu = F.copy()
+        Fu[np.triu_indices(n, 1)] = 0
+        np.fill_diagonal(Fu, ONE)  # U = I, so U^T y = b leaves y = b
+        ipiv = np.arange(1, n + 1, dtype=np.int32)
+        want = oracle.rgetrs(Fu, ipiv, B, trans="T")
+        dF = to_dev(Fu)
+        binding.posit_rgetrs("T", n, nrhs, dF, n, torch.from_numpy(ipiv).to(DEV), dB, n)
+    else:
+        want = oracle.rpotrs(F, B, uplo="L")
+        binding.posit_rpotrs("L", n, nrhs, dF, n, dB, n)
+    torch.cuda.synchronize()
+    assert_same(from_dev(dB), want, f"{kind} {case}")
 
 
 def test_solve_workload_2048():
