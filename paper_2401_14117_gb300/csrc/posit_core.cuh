@@ -346,10 +346,11 @@ static __device__ __forceinline__ void pz_add_exact_inband_t(pz c, pz t, uint32_
   uint32_t shv = __funnelshift_rc(magS, 0u, d);   // magS >> d, 0 from 32 on
   uint32_t lost = __funnelshift_rc(0u, magS, d);  // the bits shifted out
   shv |= min(lost, 1u);
-  const bool sub = (int)(mL ^ mS) < 0;
-  const int Rd = (int)(magL - shv);  // in (-2^31, 2^31); negative only when d = 0
-  const uint32_t R = sub ? (uint32_t)abs(Rd) : (magL + shv);
-  sign = (mL ^ ((sub && Rd < 0) ? 0x80000000u : 0u)) & 0x80000000u;
+  uint32_t sub = (mL ^ mS) >> 31;
+  uint32_t R = sub ? (magL - shv) : (magL + shv);
+  uint32_t neg = sub & (R >> 31);  // difference went negative (d = 0 only)
+  R = neg ? (0u - R) : R;
+  sign = (mL & 0x80000000u) ^ (neg << 31);
   const uint32_t lz = pz_lead_shift(R);
   // lead at bit 31 (R << lz; 0 for R = 0), then back to bit 30 with the bit
   // shifted out jammed (it can only be nonzero when lz = 0)
