@@ -44,12 +44,12 @@ ONE = 0x40000000
 # inner loop, so they scale with M N K): integer-ALU-pipe warp instructions
 # (sm__inst_executed_pipe_alu.sum / M N K) and all warp instructions
 # (smsp__inst_executed.sum / M N K).
-ALU_INST_PER_MAC = 1.1273  # 6.19745e11 / 5.49756e11 (NN 8192^3)
-INST_PER_MAC = 2.0086      # 1.10426e12 / 5.49756e11
-FMA_INST_PER_MAC = 0.7464  # sm__inst_executed_pipe_fmaheavy.sum: 4.10328e11 / 5.49756e11
+ALU_INST_PER_MAC = 1.0648  # 5.85386e11 / 5.49756e11 (NN 8192^3)
+INST_PER_MAC = 2.0067      # 1.10319e12 / 5.49756e11
+FMA_INST_PER_MAC = 0.8069  # sm__inst_executed_pipe_fmaheavy.sum: 4.43614e11 / 5.49756e11
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one captured
 # 8192^3 launch.
-TRAFFIC_8192 = 4.98842e9 + 0.42116e9
+TRAFFIC_8192 = 4.99843e9 + 0.42177e9
 # The kernel is bound by the integer ALU pipe: 16 lanes per scheduler, i.e.
 # 0.5 warp instruction per clock per scheduler (the rate at which ncu's
 # sm__inst_executed_pipe_alu.avg.pct_of_peak_sustained_active reads 100 %).

@@ -190,6 +190,20 @@ static __device__ __forceinline__ pz pz_round_apply(const pz_rtab &e, uint32_t s
   return pz{S + (int)c, pz_imad(c, e.carry, rs)};
 }
 
+// pz_round_apply of (X0 | jam) with the jam put into the tie bit instead:
+// rounding drops the part D = X mod 2^q and carries into bit q exactly when
+// D > 2^(q-1), or D = 2^(q-1) and (the lsb is odd or nonzero bits lie below
+// bit 0); with hm1 = 2^(q-1) - 1 that is D + hm1 + (lsb | jam) >= 2^q, the
+// same carry as (D | jam) + hm1 + lsb, one logic instruction fewer.
+static __device__ __forceinline__ pz pz_round_apply_jam(const pz_rtab &e, uint32_t sign, int S,
+                                                        uint32_t X0, uint32_t jam) {
+  const uint32_t lsb = (pz_imad(X0, e.tie, 0u) >> 31) | jam;
+  const uint32_t rf = X0 + e.hm1 + lsb;
+  const uint32_t rs = (rf & e.keep) ^ sign;
+  const uint32_t c = rf >> 31;
+  return pz{S + (int)c, pz_imad(c, e.carry, rs)};
+}
+
 // pz_round_tab without the test for the regimes of 28 or more bits: only for
 // values whose scale is in [-108, 107] or that are zero (significand 0), with
 // the table of pz_rtab_inband_entry.
@@ -220,19 +234,27 @@ static __device__ __forceinline__ pz pz_neg(pz a) {
 // The 28x28-bit significand product is exact in 64 bits; its leading one
 // lands at bit 61 or 62.
 // The unrounded product: sign, scale and significand (lead at bit 30, jam).
-static __device__ __forceinline__ void pz_mul_exact(pz a, pz b, uint32_t &sign, int &S,
-                                                    uint32_t &X) {
+static __device__ __forceinline__ void pz_mul_parts(pz a, pz b, uint32_t &sign, int &S,
+                                                    uint32_t &X0, uint32_t &jam) {
   uint32_t A = a.m & 0x7FFFFFFFu;  // leading one at bit 30 (or 0)
   uint32_t B = b.m << 1;           // leading one at bit 31 (or 0)
   uint64_t P = (uint64_t)A * (uint64_t)B;
   uint32_t hi = (uint32_t)(P >> 32), lo = (uint32_t)P;
   uint32_t t = hi >> 30;           // 1 if the leading one is at bit 62
   // leading one to bit 30: hi, or 2 hi = hi * (t ^ 1) + hi (a multiply-add);
-  // every bit of lo is jammed into bit 0 (below the guard bit, so the lo bit
-  // that a shift by one would bring in needs no special care)
-  X = pz_imad(hi, t ^ 1u, hi) | min(lo, 1u);
+  // the bits of lo only matter as the jam (the lo bit that a shift by one
+  // would bring in lies below the guard bit, so it needs no special care)
+  X0 = pz_imad(hi, t ^ 1u, hi);
+  jam = min(lo, 1u);
   S = a.s + b.s + (int)t;
   sign = (a.m ^ b.m) & 0x80000000u;
+}
+
+static __device__ __forceinline__ void pz_mul_exact(pz a, pz b, uint32_t &sign, int &S,
+                                                    uint32_t &X) {
+  uint32_t X0, jam;
+  pz_mul_parts(a, b, sign, S, X0, jam);
+  X = X0 | jam;
 }
 
 static __device__ __forceinline__ pz pz_mul_fast(pz a, pz b) {
@@ -243,17 +265,19 @@ static __device__ __forceinline__ pz pz_mul_fast(pz a, pz b) {
 }
 
 static __device__ __forceinline__ pz pz_mul_inband(const pz_rtab *tab, pz a, pz b) {
-  uint32_t sign, X;
+  uint32_t sign, X0, jam;
   int S;
-  pz_mul_exact(a, b, sign, S, X);
-  return pz_round_inband(tab, sign, S, X);
+  pz_mul_parts(a, b, sign, S, X0, jam);
+  return pz_round_apply_jam(tab[S & 255], sign, S, X0, jam);
 }
 
 static __device__ __forceinline__ pz pz_mul_tab(const pz_rtab *tab, pz a, pz b) {
-  uint32_t sign, X;
+  uint32_t sign, X0, jam;
   int S;
-  pz_mul_exact(a, b, sign, S, X);
-  return pz_round_tab(tab, sign, S, X);
+  pz_mul_parts(a, b, sign, S, X0, jam);
+  const pz_rtab e = tab[min((unsigned)(S + 128), 255u)];
+  if (e.tie == 0u) return pz_round(sign, S, X0 | jam);
+  return pz_round_apply_jam(e, sign, S, X0, jam);
 }
 
 // c (+) t, one rounding, for operands that are not NaR.  Sign-magnitude add
