@@ -456,9 +456,10 @@ static __device__ __forceinline__ pz pz_add_serial(pz c, pz t) {
   const uint32_t hm1 = c0 ? kA.hm1 : (c1 ? kB.hm1 : kC.hm1);
   const uint32_t keep = c0 ? kA.keep : (c1 ? kB.keep : kC.keep);
   const int S = c0 ? SL + 1 : (c1 ? SL : SL - 1);
-  const uint32_t r = (X + hm1 + lsb) & keep;
-  const uint32_t cy = r >> 31;
-  pz res{S + (int)cy, sign | (r >> cy)};
+  // a round-up that carries out of the significand gives exactly 2^(S+1)
+  const uint32_t rf = X + hm1 + lsb;
+  const bool cy = rf >= 0x80000000u;
+  pz res{cy ? S + 1 : S, cy ? (sign | 0x40000000u) : (sign | (rf & keep))};
   const bool slow = (sub && (int)Rs < 0) || R < 0x20000000u || (unsigned)(SL + 107) > 213u;
   if (slow) res = pz_add_fast(c, t);
   return res;
