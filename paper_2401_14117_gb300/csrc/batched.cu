@@ -423,6 +423,7 @@ __device__ void potrs_decoded(const pz *M, int n, pz *X, int nrhs, pz *prod) {
       bool nar = pz_is_nar(acc);
       const pz *pr = prod + c * m;
       pz pn = pr[0];
+#pragma unroll 4
       for (int t = 0; t < m; ++t) {
         const pz p = pn;
         pn = pr[t + 1];  // loaded ahead; prod holds n * max(nrhs, 1) > m * nrhs entries

@@ -420,13 +420,17 @@ static __device__ __forceinline__ pz pz_add_tab(const pz_rtab *tab, pz c, pz t) 
 // one bit of cancellation -- are formed side by side from the sum, each with
 // the rounding constants of its scale (SL + 1, SL, SL - 1, computed from the
 // larger scale SL while the sum is formed), and the sum's magnitude picks
-// one.  The rare cases go to pz_add_fast: a difference that went negative or
-// cancelled more than one bit (zero included), and a larger scale outside
-// [-107, 106], whose neighbours may have a regime of 28 or more bits (zero and
-// NaR operands have scales far outside).
+// one.  The rare cases go to pz_add_fast, out of line: a difference that went
+// negative or cancelled more than one bit (zero included), and a larger scale
+// outside [-107, 106], whose neighbours may have a regime of 28 or more bits
+// (zero and NaR operands have scales far outside).
 struct pz_rq {
   uint32_t hm1, keep, q;
 };
+
+// pz_add_fast out of line: the rare fallback of pz_add_serial, kept out of
+// the chain's straight-line code.
+static __device__ __noinline__ pz pz_add_fast_call(pz c, pz t) { return pz_add_fast(c, t); }
 
 // Rounding constants of a scale whose regime is shorter than 28 bits.
 static __device__ __forceinline__ pz_rq pz_rq_of(int S) {
@@ -461,7 +465,7 @@ static __device__ __forceinline__ pz pz_add_serial(pz c, pz t) {
   const bool cy = rf >= 0x80000000u;
   pz res{cy ? S + 1 : S, cy ? (sign | 0x40000000u) : (sign | (rf & keep))};
   const bool slow = (sub && (int)Rs < 0) || R < 0x20000000u || (unsigned)(SL + 107) > 213u;
-  if (slow) res = pz_add_fast(c, t);
+  if (slow) res = pz_add_fast_call(c, t);
   return res;
 }
 

@@ -229,6 +229,7 @@ __global__ void __launch_bounds__(ST) trsv_dot_backward_kernel(const uint32_t *_
         const int cnt = (int)min64(ST, n - k0);
         const pz *pr = prod[buf];
         pz pn = pr[0];
+#pragma unroll 4
         for (int t = 0; t < cnt; ++t) {
           const pz p = pn;
           pn = pr[t + 1];  // next link's product, loaded ahead (row padded by one)
