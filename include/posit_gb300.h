@@ -234,6 +234,24 @@ POSIT_API int posit_factor_solve_batched(int64_t count, const posit_problem *pro
                                          const posit_plan *plan, void *workspace,
                                          cudaStream_t stream);
 
+/* Autotuner of the batched launch shape: times posit_factor_solve_batched on
+ * `problems` (a DEVICE descriptor array, as above, with `order` as above)
+ * under each of the `ncand` candidate plans in the HOST array `cands` and
+ * writes the fastest to *best (HOST).  times_ms (HOST, ncand floats, or NULL)
+ * receives each candidate's best time of `reps` runs, -1 for a plan that
+ * could not be launched (e.g. more shared memory than an SM has).  Since
+ * every plan computes the same bits, only time is compared; ties go to the
+ * plan with fewer threads per SM.  The problems are not modified: the timed
+ * runs work on device copies of A and B (stream-ordered allocations made and
+ * freed inside the call).  Blocks until `stream` has finished.
+ * Errors: -1 count (must be > 0), -2 problems NULL, -4 max_n, -5 max_nrhs,
+ * -6 cands NULL or ncand < 1, -8 reps < 1, -9 best NULL; POSIT_ERR_ALLOC if
+ * the copies do not fit; POSIT_ERR_CUDA if no candidate could be launched. */
+POSIT_API int posit_autotune(int64_t count, const posit_problem *problems, const int32_t *order,
+                             int64_t max_n, int64_t max_nrhs, const posit_plan *cands,
+                             int32_t ncand, int32_t reps, posit_plan *best, float *times_ms,
+                             cudaStream_t stream);
+
 /* ---------------------------------------------------------------------------
  * Serving: a continuous-batching server for factor+solve requests (the
  * request-serving pattern over the paper's Rgetrf+Rgetrs / Rpotrf+Rpotrs).

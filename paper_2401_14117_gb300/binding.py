@@ -38,6 +38,8 @@ _SIGS = {
     "posit_rpotrs": [c_char, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp],
     "posit_batched_workspace_size": [c_i64, c_i64, c_vp, c_vp],
     "posit_factor_solve_batched": [c_i64, c_vp, c_vp, c_i64, c_i64, c_vp, c_vp, c_vp],
+    "posit_autotune": [c_i64, c_vp, c_vp, c_i64, c_i64, c_vp, ctypes.c_int32, ctypes.c_int32,
+                       c_vp, c_vp, c_vp],
     "posit_serve_open": [c_vp, c_vp],
     "posit_serve_submit": [c_vp, c_vp],
     "posit_serve_poll": [c_vp, c_vp, c_i64, c_vp],
@@ -197,6 +199,19 @@ def posit_factor_solve_batched(count, problems, order, max_n, max_nrhs, plan, wo
     return _check("posit_factor_solve_batched", lib().posit_factor_solve_batched(
         count, _ptr(problems), _ptr(order), max_n, max_nrhs, ctypes.byref(plan),
         _ptr(workspace), _stream(stream)))
+
+
+def posit_autotune(count, problems, order, max_n, max_nrhs, cands, reps=1, stream=None):
+    """Fastest of the candidate plans (a list of posit_plan) on the batch;
+    returns (best posit_plan, list of per-candidate ms, -1 where a plan could
+    not be launched).  The problems' arrays are left unchanged."""
+    arr = (posit_plan * len(cands))(*cands)
+    times = (ctypes.c_float * len(cands))()
+    best = posit_plan()
+    _check("posit_autotune", lib().posit_autotune(
+        count, _ptr(problems), _ptr(order), max_n, max_nrhs, ctypes.byref(arr), len(cands), reps,
+        ctypes.byref(best), ctypes.byref(times), _stream(stream)))
+    return best, [float(t) for t in times]
 
 
 def posit_serve_open(cfg):

@@ -10,6 +10,9 @@
 // of Rgetrf/Rpotrf and the trsm orders of Rgetrs/Rpotrs (see
 // include/posit_gb300.h), so every result equals the plain routines' result
 // bit for bit, whatever the plan.
+#include <algorithm>
+#include <vector>
+
 #include "internal.cuh"
 
 namespace posit {
@@ -610,4 +613,165 @@ extern "C" int posit_factor_solve_batched(int64_t count, const posit_problem *pr
     return st;
   }
   return batched_launch(problems, order, count, (int)max_n, (int)max_nrhs, *plan, workspace, stream);
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the launch shape.  The problems' A and B are packed once into a
+// pristine copy; before every timed run the working copy is restored from it
+// with one device-to-device copy, so each run factors the same inputs and the
+// caller's arrays are never written.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct TuneArena {
+  void *p = nullptr;
+  cudaStream_t s = nullptr;
+  ~TuneArena() {
+    if (p) cudaFreeAsync(p, s);
+  }
+};
+
+bool plan_less(const posit_plan &a, float ta, const posit_plan &b, float tb) {
+  if (ta != tb) return ta < tb;
+  const int64_t wa = (int64_t)a.threads * a.ctas_per_sm, wb = (int64_t)b.threads * b.ctas_per_sm;
+  if (wa != wb) return wa < wb;
+  return a.smem_bytes < b.smem_bytes;
+}
+
+}  // namespace
+
+extern "C" int posit_autotune(int64_t count, const posit_problem *problems, const int32_t *order,
+                              int64_t max_n, int64_t max_nrhs, const posit_plan *cands,
+                              int32_t ncand, int32_t reps, posit_plan *best, float *times_ms,
+                              cudaStream_t stream) {
+  if (count <= 0) return -1;
+  if (!problems) return -2;
+  if (max_n < 0 || max_n > 46340) return -4;
+  if (max_nrhs < 0) return -5;
+  if (!cands || ncand < 1) return -6;
+  if (reps < 1) return -8;
+  if (!best) return -9;
+
+  // the caller's descriptors, checked before anything is copied
+  std::vector<posit_problem> hp((size_t)count);
+  if (cudaMemcpyAsync(hp.data(), problems, sizeof(posit_problem) * (size_t)count,
+                      cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+      cudaStreamSynchronize(stream) != cudaSuccess)
+    return POSIT_ERR_CUDA;
+  size_t words = 0;  // A and B of every problem, packed with ld = n
+  for (const posit_problem &q : hp) {
+    if (q.n < 0 || q.n > max_n || q.nrhs < 0 || q.nrhs > max_nrhs || q.lda < (q.n > 0 ? q.n : 1) ||
+        q.ldb < (q.n > 0 ? q.n : 1) || !q.A || (q.nrhs > 0 && !q.B) ||
+        (q.kind != POSIT_LU && q.kind != POSIT_CHOLESKY && q.kind != POSIT_CHOLESKY_U))
+      return -2;
+    words += (size_t)q.n * q.n + (size_t)q.n * q.nrhs;
+  }
+  size_t ipiv_words = 0;
+  for (const posit_problem &q : hp) ipiv_words += (size_t)q.n;
+
+  size_t ws_bytes = 0;
+  for (int32_t c = 0; c < ncand; ++c)
+    if (plan_ok(&cands[c]))
+      ws_bytes = std::max(ws_bytes, batched_workspace_bytes((int)max_n, (int)max_nrhs, cands[c]));
+  if (ws_bytes == 0) return POSIT_ERR_CUDA;
+
+  // one allocation: pristine A/B | working A/B | ipiv | info | descriptors | workspace
+  auto up16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
+  const size_t ab_bytes = up16(words * 4);
+  const size_t off_work = ab_bytes, off_ipiv = 2 * ab_bytes;
+  const size_t off_info = off_ipiv + up16(ipiv_words * 4);
+  const size_t off_desc = off_info + up16((size_t)count * 4);
+  const size_t off_ws = off_desc + up16(sizeof(posit_problem) * (size_t)count);
+  const size_t total = off_ws + ws_bytes;
+  TuneArena arena;
+  arena.s = stream;
+  if (cudaMallocAsync(&arena.p, total, stream) != cudaSuccess) {
+    arena.p = nullptr;
+    cudaGetLastError();
+    return POSIT_ERR_ALLOC;
+  }
+  char *base = static_cast<char *>(arena.p);
+  uint32_t *pristine = reinterpret_cast<uint32_t *>(base);
+  uint32_t *work = reinterpret_cast<uint32_t *>(base + off_work);
+  int32_t *ipiv = reinterpret_cast<int32_t *>(base + off_ipiv);
+  int32_t *info = reinterpret_cast<int32_t *>(base + off_info);
+  posit_problem *desc = reinterpret_cast<posit_problem *>(base + off_desc);
+  void *ws = base + off_ws;
+
+  std::vector<posit_problem> wp((size_t)count);
+  size_t w = 0, ip = 0;
+  for (size_t i = 0; i < hp.size(); ++i) {
+    const posit_problem &q = hp[i];
+    posit_problem &r = wp[i];
+    r = q;
+    const int64_t n = q.n, ld = n > 0 ? n : 1;
+    r.lda = ld;
+    r.ldb = ld;
+    r.A = work + w;
+    if (n > 0 && cudaMemcpy2DAsync(pristine + w, (size_t)n * 4, q.A, (size_t)q.lda * 4,
+                                   (size_t)n * 4, (size_t)n, cudaMemcpyDeviceToDevice,
+                                   stream) != cudaSuccess)
+      return POSIT_ERR_CUDA;
+    w += (size_t)n * n;
+    r.B = q.nrhs > 0 ? work + w : nullptr;
+    if (n > 0 && q.nrhs > 0 &&
+        cudaMemcpy2DAsync(pristine + w, (size_t)n * 4, q.B, (size_t)q.ldb * 4, (size_t)n * 4,
+                          (size_t)q.nrhs, cudaMemcpyDeviceToDevice, stream) != cudaSuccess)
+      return POSIT_ERR_CUDA;
+    w += (size_t)n * q.nrhs;
+    r.ipiv = ipiv + ip;
+    ip += (size_t)n;
+    r.info = info + i;
+  }
+  if (cudaMemcpyAsync(desc, wp.data(), sizeof(posit_problem) * (size_t)count,
+                      cudaMemcpyHostToDevice, stream) != cudaSuccess)
+    return POSIT_ERR_CUDA;
+
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return POSIT_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return POSIT_ERR_CUDA;
+  }
+  int found = -1;
+  float found_ms = 0.0f;
+  int status = POSIT_OK;
+  for (int32_t c = 0; c < ncand && status == POSIT_OK; ++c) {
+    float t_best = -1.0f;
+    if (plan_ok(&cands[c])) {
+      for (int32_t r = 0; r < reps; ++r) {
+        if (cudaMemcpyAsync(work, pristine, words * 4, cudaMemcpyDeviceToDevice, stream) !=
+                cudaSuccess ||
+            cudaEventRecord(e0, stream) != cudaSuccess) {
+          status = POSIT_ERR_CUDA;
+          break;
+        }
+        const int st = batched_launch(desc, order, count, (int)max_n, (int)max_nrhs, cands[c], ws,
+                                      stream);
+        if (st != POSIT_OK) {  // e.g. more shared memory than a CTA may have
+          cudaGetLastError();
+          t_best = -1.0f;
+          break;
+        }
+        float ms = 0.0f;
+        if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+          status = POSIT_ERR_CUDA;
+          break;
+        }
+        if (t_best < 0.0f || ms < t_best) t_best = ms;
+      }
+    }
+    if (times_ms) times_ms[c] = t_best;
+    if (t_best >= 0.0f && (found < 0 || plan_less(cands[c], t_best, cands[found], found_ms))) {
+      found = c;
+      found_ms = t_best;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (status != POSIT_OK) return status;
+  if (found < 0) return POSIT_ERR_CUDA;
+  *best = cands[found];
+  return cudaStreamSynchronize(stream) == cudaSuccess ? POSIT_OK : POSIT_ERR_CUDA;
 }

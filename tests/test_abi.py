@@ -42,3 +42,23 @@ def test_product_code_does_not_touch_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "posit_oracle" not in text, f
+
+
+def test_autotune_argument_errors_need_no_device():
+    """posit_autotune rejects bad arguments before any CUDA call."""
+    plan = binding.posit_plan(256, 1, 48 * 1024, 0)
+    cases = [((0, None, None, 1, 1, [plan]), -1), ((1, None, None, 1, 1, [plan]), -2),
+             ((1, 16, None, -1, 1, [plan]), -4), ((1, 16, None, 1, -1, [plan]), -5)]
+    for args, code in cases:
+        try:
+            binding.posit_autotune(*args, reps=1, stream=0)
+        except binding.PositError as e:
+            assert e.code == code, (args, e.code)
+        else:
+            raise AssertionError(f"{args} accepted")
+    try:
+        binding.posit_autotune(1, 16, None, 1, 1, [plan], reps=0, stream=0)
+    except binding.PositError as e:
+        assert e.code == -8
+    else:
+        raise AssertionError("reps = 0 accepted")

@@ -208,3 +208,28 @@ def test_batched_argument_errors():
         binding.posit_factor_solve_batched(0, None, None, 1, 1, plan_of(100, 1, 0), None)
     assert e.value.code == -6
     binding.posit_factor_solve_batched(0, None, None, 0, 0, plan, None)
+
+
+def test_native_autotune_picks_the_fastest_and_leaves_inputs():
+    """posit_autotune times every candidate on copies: the caller's arrays
+    are unchanged, an invalid plan is reported as -1, the plan returned is
+    the fastest one, and it gives the oracle's bits."""
+    rng = np.random.default_rng(9)
+    count = 24
+    ns = rng.integers(8, 160, count)
+    kinds = np.array([(L, C, CU)[i % 3] for i in range(count)], np.int32)
+    nrhs = rng.integers(0, 3, count)
+    ps, host = make_set(kinds, ns, nrhs, 300)
+    A0, B0 = ps.A.clone(), ps.B.clone()
+    cands = [plan_of(*p) for p in PLANS] + [plan_of(33, 1, 0)]
+    best, times = binding.posit_autotune(ps.count, ps.desc, ps.order, ps.max_n, ps.max_nrhs,
+                                         cands, reps=2)
+    torch.cuda.synchronize()
+    assert times[-1] == -1 and all(t > 0 for t in times[:-1]), times
+    got = (best.threads, best.ctas_per_sm, best.smem_bytes)
+    assert got in PLANS
+    assert times[PLANS.index(got)] == min(times[:-1])
+    assert torch.equal(ps.A, A0) and torch.equal(ps.B, B0)
+    ps.run(best)
+    torch.cuda.synchronize()
+    check(ps, host)
