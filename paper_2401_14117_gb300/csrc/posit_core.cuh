@@ -133,9 +133,13 @@ static __device__ __forceinline__ pz pz_round(uint32_t sign, int S, uint32_t X) 
 // of two read from a table) instead of turning it back into shifts and adds
 // on the ALU pipe, which is the one the multiply-add loops are bound by.
 static __device__ __forceinline__ uint32_t pz_imad(uint32_t a, uint32_t b, uint32_t c) {
+#ifdef __CUDA_ARCH__
   uint32_t d;
   asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
   return d;
+#else  // host compilation of this header (the arithmetic identity tests)
+  return a * b + c;
+#endif
 }
 
 // Rounding constants per scale, for kernels that keep a 256-entry table in
@@ -325,9 +329,16 @@ static __device__ __forceinline__ pz pz_add_fast(pz c, pz t) {
 // zeros) for x != 0, and 0xFFFFFFFF for x = 0: one bfind instruction, without
 // the fix-up that makes a count of leading zeros return 32 for 0.
 static __device__ __forceinline__ uint32_t pz_lead_shift(uint32_t x) {
+#ifdef __CUDA_ARCH__
   uint32_t d;
   asm("bfind.shiftamt.u32 %0, %1;" : "=r"(d) : "r"(x));
   return d;
+#else  // host compilation of this header (the arithmetic identity tests)
+  uint32_t d = 0;
+  if (x == 0u) return 0xFFFFFFFFu;
+  while (!(x & 0x80000000u)) { x <<= 1; ++d; }
+  return d;
+#endif
 }
 
 // pz_add_exact for the in-band path: clamping funnel shifts instead of
