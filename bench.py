@@ -150,6 +150,26 @@ def oracle_sample_rate(m, n, k, seconds, seed=20240126):
         cols = min(n, threads * max(1, int(round(cols * grow / threads))))
 
 
+def oracle_one_thread_rate(m, k, seed=20240127):
+    """The CPU oracle on one thread: one whole column of C (m x 1 x k)."""
+    import numpy as np
+
+    import oracle
+    from paper_2401_14117_gb300 import inputs
+    threads = oracle.get_threads()
+    A = oracle.from_double_array(inputs.uniform((m, k), seed))
+    B = oracle.from_double_array(np.random.default_rng(seed).uniform(-1, 1, (k, 1)))
+    C = np.zeros((m, 1), np.uint32)
+    oracle.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle.rgemm("N", "N", ONE, A, B, 0, C)
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(threads)
+    return 2 * m * k / dt / 1e9
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -374,7 +394,8 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, sample = oracle_sample_rate(m, n, k, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores,
-                                "kind": "oracle", "sample": sample}
+                                "kind": "oracle", "sample": sample,
+                                "one_thread_value": oracle_one_thread_rate(m, k)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
