@@ -6,6 +6,9 @@
 //   * pz_add_inband, pz_add_inband_blend (in band)   == pz_add_fast, through the
 //     rounding (the zero scale may differ: both are far below every real scale)
 //   * pz_round_apply on every in-band table row       == pz_round
+//   * Rgemm's in-band multiply-add chains (operand scales in [-40, 40], start
+//     in [-80, 80]) == the general multiply-add chain, at every step: the
+//     in-band path relies on such chains never reaching the long-regime band
 // Operands are drawn from several families (any word; near cancellation;
 // near equality; |x| near 1; long regimes; exact zeros).  Usage:
 //   core_identities [pairs]   -> prints one line, exit status 0 when all agree.
@@ -66,7 +69,36 @@ int main(int argc, char **argv) {
     const uint32_t sg = (g() & 1) ? 0x80000000u : 0u;
     if (!same(pz_round_apply(tin[S & 255], sg, S, X), pz_round(sg, S, X))) ++bad_round;
   }
-  printf("pairs %ld (in band %ld): serial add %ld, multiply %ld, in-band add %ld, rounding %ld "
-         "mismatches\n", pairs, n_ib, bad_serial, bad_mul, bad_add_ib, bad_round);
-  return (bad_serial || bad_mul || bad_add_ib || bad_round) ? 1 : 0;
+  // accumulation chains with operands at the band's extremes: products near
+  // 2^+-80 and sums that grow towards the 2^88 bound or cancel
+  long bad_chain = 0, chain_steps = 0;
+  const int chains = (int)(pairs / 20000) + 1;
+  for (int ch = 0; ch < chains; ++ch) {
+    const int K = 256 << (ch % 6);  // 256 .. 8192
+    const int mode = ch % 4;
+    auto operand = [&](void) {
+      // a posit of scale lo..hi (or zero one time in 64), rounded from a double
+      // of binade lo..hi-1 (rounding up can reach 2^hi, not beyond)
+      const int lo = mode == 0 ? 30 : -40, hi = mode == 1 ? -30 : 40;
+      if ((g() & 63) == 0) return pz_zero();
+      const int e = lo + (int)(g() % (uint64_t)(hi - lo));
+      const double v = std::ldexp(1.0 + (double)(g() >> 11) * 0x1p-53, e);
+      const uint32_t w = pz_from_double((g() & 1) ? -v : v);
+      return pz_decode(w);
+    };
+    pz accF = pz_zero(), accI = pz_zero();
+    if (mode == 2) accF = accI = pz{80, 0x40000000u};          // start at 2^80
+    for (int k = 0; k < K; ++k) {
+      pz a = operand(), b = operand();
+      if (mode == 3 && (k & 1)) { b = a; a = pz_one(); a.m ^= 0x80000000u; }  // x - x patterns
+      accF = pz_add_fast(accF, pz_mul_fast(b, a));
+      accI = pz_add_inband_blend(tin, 0xFFFFFFFFu, accI, pz_mul_inband(tin, b, a));
+      ++chain_steps;
+      if (!same_value(accF, accI)) { ++bad_chain; break; }
+    }
+  }
+  printf("pairs %ld (in band %ld): serial add %ld, multiply %ld, in-band add %ld, rounding %ld, "
+         "chains %ld mismatches (%ld chain steps)\n", pairs, n_ib, bad_serial, bad_mul,
+         bad_add_ib, bad_round, bad_chain, chain_steps);
+  return (bad_serial || bad_mul || bad_add_ib || bad_round || bad_chain) ? 1 : 0;
 }

@@ -25,7 +25,7 @@ def test_fast_forms_equal_general_forms(tmp_path):
                     os.path.join(HERE, "c", "core_identities.cpp")], check=True)
     r = subprocess.run([str(exe), "20000000"], capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stdout + r.stderr
-    assert "serial add 0, multiply 0, in-band add 0, rounding 0" in r.stdout, r.stdout
+    assert "serial add 0, multiply 0, in-band add 0, rounding 0, chains 0" in r.stdout, r.stdout
 
 
 @pytest.mark.skipif(shutil.which("g++") is None, reason="needs g++")
