@@ -237,7 +237,9 @@ static __device__ __forceinline__ pz pz_neg(pz a) {
 // magnitude 0 gives a zero product whose scale stays far below real ones).
 // The 28x28-bit significand product is exact in 64 bits; its leading one
 // lands at bit 61 or 62.
-// The unrounded product: sign, scale and significand (lead at bit 30, jam).
+// The unrounded product: sign, scale, the significand X0 (lead at bit 30) and
+// the jam (1 when nonzero bits lie below X0's bit 0); pz_mul_exact ORs the
+// jam into bit 0, pz_round_apply_jam takes it apart.
 static __device__ __forceinline__ void pz_mul_parts(pz a, pz b, uint32_t &sign, int &S,
                                                     uint32_t &X0, uint32_t &jam) {
   uint32_t A = a.m & 0x7FFFFFFFu;  // leading one at bit 30 (or 0)
