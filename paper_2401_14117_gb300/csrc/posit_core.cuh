@@ -469,7 +469,8 @@ static __device__ __forceinline__ pz pz_add_serial(pz c, pz t) {
   const pz_rq kA = pz_rq_of(SL + 1), kB = pz_rq_of(SL), kC = pz_rq_of(SL - 1);
   const bool c0 = R >= 0x80000000u, c1 = R >= 0x40000000u;  // carry / no shift / one bit
   const uint32_t X = c0 ? ((R >> 1) | (R & 1u)) : (c1 ? R : R << 1);
-  const uint32_t lsb = c0 ? (R >> (kA.q + 1u)) & 1u : (c1 ? (R >> kB.q) & 1u : (R >> (kC.q - 1u)) & 1u);
+  const uint32_t lsb = c0 ? (R >> (kA.q + 1u)) & 1u
+                          : (c1 ? (R >> kB.q) & 1u : (R >> (kC.q - 1u)) & 1u);
   const uint32_t hm1 = c0 ? kA.hm1 : (c1 ? kB.hm1 : kC.hm1);
   const uint32_t keep = c0 ? kA.keep : (c1 ? kB.keep : kC.keep);
   const int S = c0 ? SL + 1 : (c1 ? SL : SL - 1);
