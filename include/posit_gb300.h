@@ -113,7 +113,12 @@ POSIT_API int posit_rgemm(char transa, char transb, int64_t m, int64_t n, int64_
  * i, k > c.  The blocked schedule (panels of up to 256 columns, trailing
  * update by Rgemm with alpha = -1, beta = 1) applies exactly these operations
  * to every element in the same order, so the result is bit-identical for
- * every block size.  Scratch: about 0.7 MB, stream-ordered.
+ * every block size.  Scratch: about 0.7 MB, stream-ordered.  The work is
+ * issued on `stream` and, from the third panel on, on a library-owned
+ * high-priority stream per device (created on the first call) that factors
+ * the next panel while `stream` updates the trailing matrix; the two are
+ * joined by events before the call returns, so the work is ordered on
+ * `stream` as usual (also under stream capture).
  * Errors: -1 m < 0, -2 n < 0, -3 A NULL, -4 lda, -5 ipiv NULL, -6 info NULL.
  * ------------------------------------------------------------------------ */
 POSIT_API int posit_rgetrf(int64_t m, int64_t n, posit32_t *A, int64_t lda, int32_t *ipiv,
@@ -146,8 +151,10 @@ POSIT_API int posit_rgetrs(char trans, int64_t n, int64_t nrhs, const posit32_t 
  * a_ij = a_ij * r (i > j); a_ik = a_ik - a_ij * a_kj for j < k <= i.  uplo
  * 'U' is the transposed mirror.  Blocked: panels of up to 256 columns, the
  * trailing triangle updated by Rgemm (alpha = -1, beta = 1); bit-identical
- * for every block size.  After a failure (info > 0) columns 0 .. info-2 hold
- * their final values and the rest of the triangle is unspecified.
+ * for every block size; the next panel is factored ahead on the library's
+ * side stream as in posit_rgetrf.  After a failure (info > 0) columns
+ * 0 .. info-2 hold their final values and the rest of the triangle is
+ * unspecified.
  * Errors: -1 uplo, -2 n, -3 A NULL, -4 lda, -5 info NULL.
  * ------------------------------------------------------------------------ */
 POSIT_API int posit_rpotrf(char uplo, int64_t n, posit32_t *A, int64_t lda, int32_t *info,
@@ -332,6 +339,24 @@ POSIT_API int posit_serve_stats(const posit_server *server, posit_serve_stats_t 
 
 /* Wait for the server's streams, free everything.  Errors: -1 server NULL. */
 POSIT_API int posit_serve_close(posit_server *server);
+
+/* ---------------------------------------------------------------------------
+ * posit_selftest_wait: failure-detection self-test of the bounded device
+ * waits.  (The paper has no counterpart; its factorisations never wait on
+ * the device.)
+ *
+ * The panel kernels of posit_rgetrf / posit_rpotrf meet at grid barriers
+ * whose waits give up after a time limit (2 s there), set an error flag,
+ * write POSIT_ERR_TIMEOUT into info and return, instead of hanging the GPU.
+ * This call runs that same barrier, with a limit of wait_ns nanoseconds, in
+ * a state where it can never complete (two CTAs waiting for a third), so the
+ * limit runs out: after the stream completes, *info (device int32) holds
+ * POSIT_ERR_TIMEOUT and the context stays usable.  Asynchronous; takes
+ * 256 bytes of stream-ordered scratch.
+ * Errors: -1 wait_ns outside [1e3, 1e10], -2 info NULL, POSIT_ERR_ALLOC,
+ * POSIT_ERR_CUDA.
+ * ------------------------------------------------------------------------ */
+POSIT_API int posit_selftest_wait(int64_t wait_ns, int32_t *info, cudaStream_t stream);
 
 /* ---------------------------------------------------------------------------
  * posit_rgetrf_static: posit_rgetrf for callers that must not allocate.

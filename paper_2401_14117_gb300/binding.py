@@ -46,6 +46,7 @@ _SIGS = {
     "posit_serve_stats": [c_vp, c_vp],
     "posit_serve_close": [c_vp],
     "posit_rgetrf_static": [c_i64, c_i64, c_vp, c_i64, c_vp, c_vp, c_vp],
+    "posit_selftest_wait": [c_i64, c_vp, c_vp],
 }
 
 POSIT_LU = 0
@@ -245,3 +246,10 @@ def posit_rgetrf_static(m, n, A, lda, ipiv, info, stream=None):
     """posit_rgetrf without any device allocation (fixed scratch in the library)."""
     return _check("posit_rgetrf_static", lib().posit_rgetrf_static(
         m, n, _ptr(A), lda, _ptr(ipiv), _ptr(info), _stream(stream)))
+
+
+def posit_selftest_wait(wait_ns, info, stream=None):
+    """Run the factorisations' bounded grid-barrier wait where it cannot
+    complete; *info becomes POSIT_ERR_TIMEOUT once the stream completes."""
+    return _check("posit_selftest_wait", lib().posit_selftest_wait(wait_ns, _ptr(info),
+                                                                    _stream(stream)))

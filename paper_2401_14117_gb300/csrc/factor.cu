@@ -16,7 +16,10 @@
 //
 // Every element receives its updates in ascending column order, one rounded
 // multiply and one rounded subtract each, exactly as the unblocked algorithm
-// does, so the result is the same for every jb.
+// does, so the result is the same for every jb.  From the third panel on the
+// next panel is factored on a second stream while the rest of the trailing
+// update runs (lookahead, getrf_run / potrf_run); the order per element is
+// unchanged.
 //
 // The panel kernel is a cooperative launch: G CTAs own contiguous chunks of
 // the panel's rows, kept decoded in shared memory for the whole panel, and
@@ -24,6 +27,8 @@
 // 2 s of global time); a CTA that gives up sets the error flag, writes
 // POSIT_ERR_TIMEOUT into info, and every CTA returns.
 #include <cooperative_groups.h>
+
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -50,9 +55,10 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
 // launch): the CTA whose arrival returns `old` waits until the counter
 // reaches the next multiple of nblocks.  One atomic per CTA and a spin on an
 // acquire load; the error flag and the clock are looked at every 256 polls,
-// and the wait gives up after about 2 s of global time.  Returns false after
-// a timeout (or another CTA's).
-__device__ bool grid_barrier(unsigned *bar, unsigned nblocks, int *err, int32_t *info) {
+// and the wait gives up after wait_ns of global time (2 s in the
+// factorisations).  Returns false after a timeout (or another CTA's).
+__device__ bool grid_barrier(unsigned *bar, unsigned nblocks, int *err, int32_t *info,
+                             unsigned long long wait_ns) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
@@ -66,7 +72,7 @@ __device__ bool grid_barrier(unsigned *bar, unsigned nblocks, int *err, int32_t 
         const unsigned long long now = global_ns();
         if (t0 == 0) {
           t0 = now;
-        } else if (now - t0 > kWaitNs) {
+        } else if (now - t0 > wait_ns) {
           atomicExch(err, 1);
           atomicExch(info, POSIT_ERR_TIMEOUT);
           break;
@@ -145,7 +151,7 @@ __global__ void __launch_bounds__(PT, 1) panel_kernel(PanelArgs a) {
   if (a.chol) {
     // diagonal value of column 0, published by the CTA owning row j
     if (g == 0 && tid == 0) a.diag[0] = tile[0];
-    if (!grid_barrier(a.bar, G, a.err, a.info)) return;
+    if (!grid_barrier(a.bar, G, a.err, a.info, kWaitNs)) return;
   }
 
   for (int c = 0; c < jb; ++c) {
@@ -192,7 +198,7 @@ __global__ void __launch_bounds__(PT, 1) panel_kernel(PanelArgs a) {
         pz *dst = a.xrow + (size_t)buf * jb;
         for (int k = tid; k < jb; k += PT) dst[k] = tile[(size_t)lrow_c * jb + k];
       }
-      if (!grid_barrier(a.bar, G, a.err, a.info)) return;
+      if (!grid_barrier(a.bar, G, a.err, a.info, kWaitNs)) return;
 
       // every CTA picks the same pivot: largest |a|, then the lowest row
       // (candidates read in parallel, then a warp / block reduction)
@@ -312,7 +318,7 @@ __global__ void __launch_bounds__(PT, 1) panel_kernel(PanelArgs a) {
           a.diag[buf ^ 1] = *x;
         }
       }
-      if (!grid_barrier(a.bar, G, a.err, a.info)) return;
+      if (!grid_barrier(a.bar, G, a.err, a.info, kWaitNs)) return;
       const int ncols = jb - c - 1;
       if (ncols > 0) {
         const pz *src = a.xrow + (size_t)buf * jb;
@@ -345,6 +351,15 @@ __global__ void __launch_bounds__(PT, 1) panel_kernel(PanelArgs a) {
     if (a.chol && gc > gr) continue;  // never touch the other triangle
     a.A[panel_addr(a, gr, gc)] = pz_to_bits(tile[(size_t)r * jb + c]);
   }
+}
+
+// One grid barrier that cannot complete: it waits for one CTA more than the
+// grid has, so every CTA's bounded wait runs out after wait_ns, sets the
+// error flag and writes POSIT_ERR_TIMEOUT into info (failure detection is
+// exercised without a fault or a hang).
+__global__ void barrier_timeout_kernel(unsigned *bar, int *err, int32_t *info,
+                                       unsigned long long wait_ns) {
+  grid_barrier(bar, gridDim.x + 1u, err, info, wait_ns);
 }
 
 // The panel's row swaps (pivots k0 .. k1-1) applied to columns [c0, c1).
@@ -584,9 +599,9 @@ struct PanelShape {
   size_t smem;
 };
 
-PanelShape panel_shape(const DeviceLimits &d, int64_t rows, int jb_want) {
+PanelShape panel_shape(const DeviceLimits &d, int64_t rows, int jb_want, int gmax) {
   PanelShape s;
-  int64_t G = min64(d.sms, max64(1, ceil_div(rows, kMinRows)));
+  int64_t G = min64(min64(d.sms, max64(1, gmax)), max64(1, ceil_div(rows, kMinRows)));
   int64_t R = ceil_div(rows, G);
   int jb = jb_want;
   // shared memory: R x jb tile + one row, decoded (8 bytes per element)
@@ -633,15 +648,85 @@ int laswp(uint32_t *A, int64_t lda, int64_t c0, int64_t c1, int64_t k0, int64_t 
 
 }  // namespace
 
+// Lookahead.  With a side stream, the factorisation runs two streams: after
+// panel j is applied (its swaps, U12 and the trailing update), the update of
+// the NEXT panel's columns is issued first, then that panel is factored on
+// the side stream while the caller's stream updates the rest of the trailing
+// matrix; the two meet (events) before the next panel's swaps.  The panel
+// and the rest touch disjoint columns, and every element still receives its
+// updates in ascending column order, so the bits are those of the one-stream
+// schedule.  The side stream has the highest priority, so the panel's CTAs
+// are scheduled ahead of the trailing Rgemm's as SMs free up.
+namespace {
+
+struct Join {
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  ~Join() {
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+  int init() {
+    for (cudaEvent_t &e : ev)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return POSIT_ERR_CUDA;
+    return POSIT_OK;
+  }
+  // `to` waits for the work issued so far on `from` (event slot k)
+  int fork(cudaStream_t from, cudaStream_t to, int k) {
+    if (cudaEventRecord(ev[k], from) != cudaSuccess) return POSIT_ERR_CUDA;
+    return cudaStreamWaitEvent(to, ev[k], 0) == cudaSuccess ? POSIT_OK : POSIT_ERR_CUDA;
+  }
+};
+
+// CTAs of a panel factored on the side stream: fewer than the SMs, so that
+// the trailing Rgemm keeps most of the GPU (measured at n = 8192: Rgetrf
+// 442 / 440 / 457 ms with 76 / 38 / 19 CTAs against 445 ms with 152;
+// Rpotrf 227 / 227 / 244 ms against 229 ms).
+constexpr int kSidePanelCtasLU = 38;
+constexpr int kSidePanelCtasChol = 76;
+
+}  // namespace
+
+// LU of the panel's columns [j, j + jb) (rows j .. m-1): sub-panels of kSub
+// columns by the cooperative kernel, the rest of the panel brought up to
+// date after each by its row swaps, a small unit-lower trsm and a rank-kSub
+// Rgemm.  Touches only the panel's columns, ipiv[j .. j+jb) and info.
+static int getrf_panel(const DeviceLimits &d, const Scratch &s, int64_t m, int64_t j, int64_t jb,
+                       uint32_t *A, int64_t lda, int32_t *ipiv, int32_t *info, int gmax,
+                       cudaStream_t stream) {
+  int st;
+  for (int64_t sp = j; sp < j + jb;) {
+    PanelShape ps = panel_shape(d, m - sp, (int)min64(kSub, j + jb - sp), gmax);
+    const int w = ps.jb;
+    PanelArgs pa{};
+    pa.A = A; pa.lda = lda; pa.m = m; pa.j = sp; pa.trans = 0; pa.chol = 0;
+    pa.ipiv = ipiv; pa.info = info;
+    pa.bar = s.bar; pa.err = s.err; pa.cand_key = s.cand_key; pa.cand_row = s.cand_row;
+    pa.cand_vals = s.cand_vals; pa.xrow = s.xrow; pa.diag = s.diag;
+    if ((st = launch_panel(pa, ps, stream))) return st;
+    // the sub-panel's swaps on the rest of the panel
+    if ((st = laswp(A, lda, j, sp, sp, sp + w, ipiv, stream))) return st;
+    if ((st = laswp(A, lda, sp + w, j + jb, sp, sp + w, ipiv, stream))) return st;
+    if (sp + w < j + jb) {
+      if ((st = trsm_llu(A, lda, sp, w, sp + w, j + jb, stream))) return st;
+      if (sp + w < m) {
+        st = rgemm_launch(false, false, TRI_FULL, m - sp - w, j + jb - sp - w, w, 0xC0000000u,
+                          A + (sp + w) + sp * lda, lda, A + sp + (sp + w) * lda, lda,
+                          PZ_ONE_BITS, A + (sp + w) + (sp + w) * lda, lda, stream);
+        if (st) return st;
+      }
+    }
+    sp += w;
+  }
+  return POSIT_OK;
+}
+
 // Blocked LU on a caller-provided scratch block (bytes from getrf_scratch_bytes).
 // Two levels: panels of up to kNB columns drive the big trailing Rgemm; each
-// panel is factored in sub-panels of kSub columns by the cooperative kernel,
-// the rest of the panel being brought up to date after each sub-panel by
-// its row swaps, a small unit-lower trsm and a rank-kSub Rgemm.  Every
-// element still receives its updates one column at a time in ascending
-// order, so the factors are those of the unblocked algorithm.
+// panel is factored by getrf_panel.  Every element still receives its
+// updates one column at a time in ascending order, so the factors are those
+// of the unblocked algorithm.  side != nullptr: lookahead on that stream.
 int getrf_run(int64_t m, int64_t n, uint32_t *A, int64_t lda, int32_t *ipiv, int32_t *info,
-              void *scratch, cudaStream_t stream) {
+              void *scratch, cudaStream_t stream, cudaStream_t side) {
   DeviceLimits d;
   int st = device_limits(d);
   if (st) return st;
@@ -650,45 +735,47 @@ int getrf_run(int64_t m, int64_t n, uint32_t *A, int64_t lda, int32_t *ipiv, int
   carve(s, scratch, d.sms, kNB);
   if (cudaMemsetAsync(scratch, 0, scratch_bytes(d.sms, kNB), stream) != cudaSuccess)
     return POSIT_ERR_CUDA;
+  const int gmax_side = kSidePanelCtasLU;
+  Join join;
+  if (side && (st = join.init())) return st;
+  bool on_side = false;  // panel j was factored on the side stream
   for (int64_t j = 0; j < mn;) {
     const int64_t jb = min64(kNB, mn - j);
-    for (int64_t sp = j; sp < j + jb;) {
-      PanelShape ps = panel_shape(d, m - sp, (int)min64(kSub, j + jb - sp));
-      const int w = ps.jb;
-      PanelArgs pa{};
-      pa.A = A; pa.lda = lda; pa.m = m; pa.j = sp; pa.trans = 0; pa.chol = 0;
-      pa.ipiv = ipiv; pa.info = info;
-      pa.bar = s.bar; pa.err = s.err; pa.cand_key = s.cand_key; pa.cand_row = s.cand_row;
-      pa.cand_vals = s.cand_vals; pa.xrow = s.xrow; pa.diag = s.diag;
-      if ((st = launch_panel(pa, ps, stream))) return st;
-      // the sub-panel's swaps on the rest of the panel
-      if ((st = laswp(A, lda, j, sp, sp, sp + w, ipiv, stream))) return st;
-      if ((st = laswp(A, lda, sp + w, j + jb, sp, sp + w, ipiv, stream))) return st;
-      if (sp + w < j + jb) {
-        if ((st = trsm_llu(A, lda, sp, w, sp + w, j + jb, stream))) return st;
-        if (sp + w < m) {
-          st = rgemm_launch(false, false, TRI_FULL, m - sp - w, j + jb - sp - w, w, 0xC0000000u,
-                            A + (sp + w) + sp * lda, lda, A + sp + (sp + w) * lda, lda,
-                            PZ_ONE_BITS, A + (sp + w) + (sp + w) * lda, lda, stream);
-          if (st) return st;
-        }
-      }
-      sp += w;
+    if (on_side) {
+      if ((st = join.fork(side, stream, 1))) return st;
+    } else if ((st = getrf_panel(d, s, m, j, jb, A, lda, ipiv, info, d.sms, stream))) {
+      return st;
     }
+    on_side = false;
     // the panel's swaps on the columns left and right of it
     if ((st = laswp(A, lda, 0, j, j, j + jb, ipiv, stream))) return st;
     if ((st = laswp(A, lda, j + jb, n, j, j + jb, ipiv, stream))) return st;
     if (j + jb < n) {
       if ((st = trsm_llu(A, lda, j, (int)jb, j + jb, n, stream))) return st;
       if (j + jb < m) {
-        st = rgemm_launch(false, false, TRI_FULL, m - j - jb, n - j - jb, jb, 0xC0000000u,
-                          A + (j + jb) + j * lda, lda, A + j + (j + jb) * lda, lda,
-                          PZ_ONE_BITS, A + (j + jb) + (j + jb) * lda, lda, stream);
+        // next panel's columns first when it is factored ahead
+        const int64_t j2 = j + jb, jb2 = min64(kNB, mn - j2);
+        const bool ahead = side && jb2 > 0 && j2 + jb2 < n;
+        const int64_t c1 = ahead ? j2 + jb2 : n;
+        st = rgemm_launch(false, false, TRI_FULL, m - j2, c1 - j2, jb, 0xC0000000u,
+                          A + j2 + j * lda, lda, A + j + j2 * lda, lda,
+                          PZ_ONE_BITS, A + j2 + j2 * lda, lda, stream);
         if (st) return st;
+        if (ahead) {
+          if ((st = join.fork(stream, side, 0))) return st;
+          if ((st = getrf_panel(d, s, m, j2, jb2, A, lda, ipiv, info, gmax_side, side)))
+            return st;
+          on_side = true;
+          st = rgemm_launch(false, false, TRI_FULL, m - j2, n - c1, jb, 0xC0000000u,
+                            A + j2 + j * lda, lda, A + j + c1 * lda, lda,
+                            PZ_ONE_BITS, A + j2 + c1 * lda, lda, stream);
+          if (st) return st;
+        }
       }
     }
     j += jb;
   }
+  if (on_side && (st = join.fork(side, stream, 1))) return st;
   return POSIT_OK;
 }
 
@@ -698,8 +785,55 @@ size_t getrf_scratch_bytes() {
   return scratch_bytes(d.sms, kNB);
 }
 
+// Cholesky of the panel's columns [j, j + jb): sub-panels of kSub columns by
+// the cooperative kernel, the rest of the panel updated by Rgemm restricted
+// to the factor's triangle.  Touches only the panel's columns (rows for
+// upper storage) and info.
+static int potrf_panel(const DeviceLimits &d, const Scratch &s, bool upper, int64_t n, int64_t j,
+                       int64_t jb, uint32_t *A, int64_t lda, int32_t *info, int gmax,
+                       cudaStream_t stream);
+
+// A(t0.., t0..c1) -= F(t0.., c0..c0+kw) F(t0..c1, c0..c0+kw)^T on the lower
+// triangle (or the transposed mirror for upper storage); skipped on the
+// device once info is set.
+static int chol_tri_update(bool upper, int64_t n, uint32_t *A, int64_t lda, int32_t *info,
+                           int64_t t0, int64_t c1, int64_t c0, int64_t kw, cudaStream_t stream) {
+  const int64_t rows = n - t0, cols = c1 - t0;
+  if (rows <= 0 || cols <= 0) return POSIT_OK;
+  if (!upper)
+    return rgemm_launch_guarded(false, true, TRI_LOWER, rows, cols, kw, 0xC0000000u,
+                                A + t0 + c0 * lda, lda, A + t0 + c0 * lda, lda, PZ_ONE_BITS,
+                                A + t0 + t0 * lda, lda, info, stream);
+  return rgemm_launch_guarded(true, false, TRI_UPPER, cols, rows, kw, 0xC0000000u,
+                              A + c0 + t0 * lda, lda, A + c0 + t0 * lda, lda, PZ_ONE_BITS,
+                              A + t0 + t0 * lda, lda, info, stream);
+}
+
+static int potrf_panel(const DeviceLimits &d, const Scratch &s, bool upper, int64_t n, int64_t j,
+                       int64_t jb, uint32_t *A, int64_t lda, int32_t *info, int gmax,
+                       cudaStream_t stream) {
+  int st;
+  for (int64_t sp = j; sp < j + jb;) {
+    PanelShape ps = panel_shape(d, n - sp, (int)min64(kSub, j + jb - sp), gmax);
+    const int w = ps.jb;
+    PanelArgs pa{};
+    pa.A = A; pa.lda = lda; pa.m = n; pa.j = sp; pa.trans = upper ? 1 : 0; pa.chol = 1;
+    pa.ipiv = nullptr; pa.info = info;
+    pa.bar = s.bar; pa.err = s.err; pa.cand_key = s.cand_key; pa.cand_row = s.cand_row;
+    pa.cand_vals = s.cand_vals; pa.xrow = s.xrow; pa.diag = s.diag;
+    if ((st = launch_panel(pa, ps, stream))) return st;
+    // rest of the panel
+    if ((st = chol_tri_update(upper, n, A, lda, info, sp + w, j + jb, sp, w, stream))) return st;
+    sp += w;
+  }
+  return POSIT_OK;
+}
+
+// Blocked Cholesky: panels of up to kNB columns by potrf_panel, the trailing
+// triangle by Rgemm restricted to the factor's triangle.  side != nullptr:
+// lookahead as in getrf_run (the next panel's columns are updated first).
 int potrf_run(bool upper, int64_t n, uint32_t *A, int64_t lda, int32_t *info, void *scratch,
-              cudaStream_t stream) {
+              cudaStream_t stream, cudaStream_t side) {
   DeviceLimits d;
   int st = device_limits(d);
   if (st) return st;
@@ -707,43 +841,58 @@ int potrf_run(bool upper, int64_t n, uint32_t *A, int64_t lda, int32_t *info, vo
   carve(s, scratch, d.sms, kNB);
   if (cudaMemsetAsync(scratch, 0, scratch_bytes(d.sms, kNB), stream) != cudaSuccess)
     return POSIT_ERR_CUDA;
-  // Panels of up to kNB columns, each factored in kSub-column sub-panels by
-  // the cooperative kernel; the rest of the panel and the trailing triangle
-  // are updated by Rgemm restricted to the factor's triangle.
-  auto tri_update = [&](int64_t t0, int64_t c1, int64_t c0, int64_t kw) -> int {
-    // A(t0.., t0..c1) -= F(t0.., c0..c0+kw) F(t0..c1, c0..c0+kw)^T on the
-    // lower triangle (or the transposed mirror for upper storage)
-    const int64_t rows = n - t0, cols = c1 - t0;
-    if (rows <= 0 || cols <= 0) return POSIT_OK;
-    if (!upper)
-      return rgemm_launch_guarded(false, true, TRI_LOWER, rows, cols, kw, 0xC0000000u,
-                                  A + t0 + c0 * lda, lda, A + t0 + c0 * lda, lda, PZ_ONE_BITS,
-                                  A + t0 + t0 * lda, lda, info, stream);
-    return rgemm_launch_guarded(true, false, TRI_UPPER, cols, rows, kw, 0xC0000000u,
-                                A + c0 + t0 * lda, lda, A + c0 + t0 * lda, lda, PZ_ONE_BITS,
-                                A + t0 + t0 * lda, lda, info, stream);
-  };
+  const int gmax_side = kSidePanelCtasChol;
+  Join join;
+  if (side && (st = join.init())) return st;
+  bool on_side = false;
   for (int64_t j = 0; j < n;) {
     const int64_t jb = min64(kNB, n - j);
-    for (int64_t sp = j; sp < j + jb;) {
-      PanelShape ps = panel_shape(d, n - sp, (int)min64(kSub, j + jb - sp));
-      const int w = ps.jb;
-      PanelArgs pa{};
-      pa.A = A; pa.lda = lda; pa.m = n; pa.j = sp; pa.trans = upper ? 1 : 0; pa.chol = 1;
-      pa.ipiv = nullptr; pa.info = info;
-      pa.bar = s.bar; pa.err = s.err; pa.cand_key = s.cand_key; pa.cand_row = s.cand_row;
-      pa.cand_vals = s.cand_vals; pa.xrow = s.xrow; pa.diag = s.diag;
-      if ((st = launch_panel(pa, ps, stream))) return st;
-      if ((st = tri_update(sp + w, j + jb, sp, w))) return st;  // rest of the panel
-      sp += w;
+    if (on_side) {
+      if ((st = join.fork(side, stream, 1))) return st;
+    } else if ((st = potrf_panel(d, s, upper, n, j, jb, A, lda, info, d.sms, stream))) {
+      return st;
     }
-    if ((st = tri_update(j + jb, n, j, jb))) return st;  // trailing triangle
+    on_side = false;
+    const int64_t j2 = j + jb, jb2 = min64(kNB, n - j2);
+    const bool ahead = side && jb2 > 0 && j2 + jb2 < n;
+    // trailing triangle: the next panel's columns first when it goes ahead
+    if ((st = chol_tri_update(upper, n, A, lda, info, j2, ahead ? j2 + jb2 : n, j, jb, stream)))
+      return st;
+    if (ahead) {
+      if ((st = join.fork(stream, side, 0))) return st;
+      if ((st = potrf_panel(d, s, upper, n, j2, jb2, A, lda, info, gmax_side, side))) return st;
+      on_side = true;
+      if ((st = chol_tri_update(upper, n, A, lda, info, j2 + jb2, n, j, jb, stream))) return st;
+    }
     j += jb;
   }
+  if (on_side && (st = join.fork(side, stream, 1))) return st;
   return POSIT_OK;
 }
 
 size_t potrf_scratch_bytes() { return getrf_scratch_bytes(); }
+
+cudaStream_t lookahead_stream() {
+  static std::mutex mu;
+  static cudaStream_t streams[64];
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!streams[dev]) {
+    int least = 0, greatest = 0;
+    cudaStream_t s = nullptr;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, greatest) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    streams[dev] = s;
+  }
+  return streams[dev];
+}
 
 }  // namespace posit
 
@@ -774,7 +923,7 @@ extern "C" int posit_rgetrf(int64_t m, int64_t n, posit32_t *A, int64_t lda, int
   void *scratch = nullptr;
   int st = with_scratch(bytes, stream, &scratch);
   if (st) return st;
-  st = getrf_run(m, n, A, lda, ipiv, info, scratch, stream);
+  st = getrf_run(m, n, A, lda, ipiv, info, scratch, stream, lookahead_stream());
   cudaFreeAsync(scratch, stream);
   return st;
 }
@@ -793,7 +942,27 @@ extern "C" int posit_rpotrf(char uplo, int64_t n, posit32_t *A, int64_t lda, int
   void *scratch = nullptr;
   int st = with_scratch(bytes, stream, &scratch);
   if (st) return st;
-  st = potrf_run(is_upper(uplo), n, A, lda, info, scratch, stream);
+  st = potrf_run(is_upper(uplo), n, A, lda, info, scratch, stream, lookahead_stream());
+  cudaFreeAsync(scratch, stream);
+  return st;
+}
+
+extern "C" int posit_selftest_wait(int64_t wait_ns, int32_t *info, cudaStream_t stream) {
+  if (wait_ns < 1000 || wait_ns > 10000000000ll) return -1;
+  if (!info) return -2;
+  if (cudaMemsetAsync(info, 0, sizeof(int32_t), stream) != cudaSuccess) return POSIT_ERR_CUDA;
+  void *scratch = nullptr;
+  int st = with_scratch(256, stream, &scratch);
+  if (st) return st;
+  unsigned *bar = static_cast<unsigned *>(scratch);
+  int *err = reinterpret_cast<int *>(bar + 2);
+  st = POSIT_OK;
+  if (cudaMemsetAsync(scratch, 0, 256, stream) != cudaSuccess) {
+    st = POSIT_ERR_CUDA;
+  } else {
+    barrier_timeout_kernel<<<2, PT, 0, stream>>>(bar, err, info, (unsigned long long)wait_ns);
+    st = launch_status();
+  }
   cudaFreeAsync(scratch, stream);
   return st;
 }

@@ -39,13 +39,18 @@ int rgemm_launch_guarded(bool ta, bool tb, int tri, int64_t m, int64_t n, int64_
                          int64_t ldc, const int32_t *abort_flag, cudaStream_t stream);
 
 // Blocked factorisations on a caller-provided scratch block of
-// getrf_scratch_bytes() / potrf_scratch_bytes() bytes (device memory).
+// getrf_scratch_bytes() / potrf_scratch_bytes() bytes (device memory).  With
+// side != nullptr the next panel is factored on `side` while the trailing
+// update runs on `stream` (lookahead; the same bits).
 size_t getrf_scratch_bytes();
 size_t potrf_scratch_bytes();
 int getrf_run(int64_t m, int64_t n, uint32_t *A, int64_t lda, int32_t *ipiv, int32_t *info,
-              void *scratch, cudaStream_t stream);
+              void *scratch, cudaStream_t stream, cudaStream_t side = nullptr);
 int potrf_run(bool upper, int64_t n, uint32_t *A, int64_t lda, int32_t *info, void *scratch,
-              cudaStream_t stream);
+              cudaStream_t stream, cudaStream_t side = nullptr);
+// The library's lookahead stream on the current device (highest priority,
+// created on first use, kept for the life of the process); nullptr on error.
+cudaStream_t lookahead_stream();
 
 // Solves on a caller-provided scratch block of solve_scratch_bytes() bytes.
 size_t solve_scratch_bytes();

@@ -64,14 +64,16 @@ extern "C" int posit_rgetrf_static(int64_t m, int64_t n, posit32_t *A, int64_t l
   if (!info) return -6;
   if (m > 0 && n > 0 && !A) return -3;
   if (m > 0 && n > 0 && !ipiv) return -5;
+  // as posit_rgetrf: info is cleared and an empty matrix returns at once,
+  // before the scratch is looked at
+  if (cudaMemsetAsync(info, 0, sizeof(int32_t), stream) != cudaSuccess) return POSIT_ERR_CUDA;
+  if (m == 0 || n == 0) return POSIT_OK;
   const size_t need = getrf_scratch_bytes();
   if (!need) return POSIT_ERR_DEVICE;
   if (need > kStaticScratchBytes) return POSIT_ERR_SCRATCH;
   void *scratch = nullptr;
   int st = static_scratch(&scratch);
   if (st) return st;
-  if (cudaMemsetAsync(info, 0, sizeof(int32_t), stream) != cudaSuccess) return POSIT_ERR_CUDA;
-  if (m == 0 || n == 0) return POSIT_OK;
   // getrf_run clears the part of the scratch that must start at zero
   return getrf_run(m, n, A, lda, ipiv, info, scratch, stream);
 }

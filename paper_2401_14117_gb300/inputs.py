@@ -11,7 +11,8 @@ matrices with mean 0 and a chosen sigma, Sec. 4 and Sec. 5):
   * scaled:   uniform in [-1, 1] times 10^u, u uniform in [-4, 4] per entry
               (long regimes, |x| up to 1e4)
   * normal:   N(0, sigma^2), the paper's generator (Sec. 4.2, Sec. 5.1)
-  * spd:      A = G G^T / n + I with G standard normal, in FP64
+  * spd:      A = G G^T / n + I with G standard normal (rounded to a
+              multiple of 2^-12, which makes G G^T exact), in FP64
   * spd_sigma: sigma^2 (G G^T / n + I), the SPD matrices of the sigma sweep
   * rhs:      b = A x_sol with x_sol = 1/sqrt(n) in every entry, in FP64
               (Sec. 5.1, error study)
@@ -43,8 +44,14 @@ def normal(shape, seed: int, sigma: float = 1.0) -> np.ndarray:
 
 
 def spd(n: int, seed: int, device=None):
-    """A = G G^T / n + I in FP64.  With a torch device, G G^T runs there."""
-    G = rng(seed).standard_normal((n, n))
+    """A = G G^T / n + I in FP64.  With a torch device, G G^T runs there.
+
+    G is standard normal rounded to a multiple of 2^-12.  Every product of two
+    entries is then a multiple of 2^-24 below 2^10 in magnitude, and every
+    partial sum of n <= 2^19 of them fits in 53 bits, so G G^T is exact: the
+    same FP64 matrix comes out on any host or device, in any summation order.
+    """
+    G = np.rint(rng(seed).standard_normal((n, n)) * 4096.0) / 4096.0
     if device is None:
         return G @ G.T / n + np.eye(n)
     import torch

@@ -15,7 +15,9 @@
  *     exact products of small integers (products, quotients, square roots).
  *
  * Usage:
- *   posit_check exhaustive <nbits> <op>        all pairs (op: add mul div sub sqrt)
+ *   posit_check exhaustive <nbits> <op> [stride offset]
+ *                                              all pairs (op: add mul div sub sqrt),
+ *                                              or first operands offset + i*stride only
  *   posit_check random <op> <count> <seed>     Posit(32,2) random pairs
  *   posit_check double <count> <seed>          Posit(32,2) from double
  *   posit_check unary32 <op> <stride>          sqrt / recip over 2^32 / stride words
@@ -298,8 +300,13 @@ int main(int argc, char **argv)
         uint32_t count = 1u << n;
         int unary = (op == OP_SQRT || op == OP_RECIP);
         uint32_t bcount = unary ? 1u : count;
+        /* optional slice: only first operands a = offset, offset + stride, ... */
+        int64_t stride = argc > 5 ? atoll(argv[4]) : 1, offset = argc > 5 ? atoll(argv[5]) : 0;
+        if (stride < 1 || offset < 0 || offset >= stride) { fprintf(stderr, "slice\n"); return 2; }
+        int64_t slices = ((int64_t)count - offset + stride - 1) / stride;
 #pragma omp parallel for schedule(dynamic, 16) reduction(+ : checked, bad)
-        for (int64_t ai = 0; ai < (int64_t)count; ai++) {
+        for (int64_t si = 0; si < slices; si++) {
+            int64_t ai = offset + si * stride;
             for (uint32_t b = 0; b < bcount; b++) {
                 checked++;
                 if (!check_one(n, op, (uint32_t)ai, b)) {

@@ -207,3 +207,39 @@ def rpotrs_lower(L, b):
             b[i] = sub(b[i], mul(L[k][i], b[k]))
         b[i] = div(b[i], L[i][i])
     return b
+
+
+def rgetrs_trans(LU, ipiv, b):
+    """A^T x = b with A = P L U (Sec. 5.1 solves, transposed): U^T y = b with
+    k ascending then a division by u_ii, the unit L^T z = y with i descending
+    and k = i+1 .. n-1 ascending, then x = P z (the swaps in reverse)."""
+    b = b[:]
+    n = len(LU)
+    for i in range(n):
+        for k in range(i):
+            b[i] = sub(b[i], mul(LU[k][i], b[k]))
+        b[i] = div(b[i], LU[i][i])
+    for i in range(n - 1, -1, -1):
+        for k in range(i + 1, n):
+            b[i] = sub(b[i], mul(LU[k][i], b[k]))
+    for i in range(n - 1, -1, -1):
+        p = ipiv[i] - 1
+        b[i], b[p] = b[p], b[i]
+    return b
+
+
+def rpotrs_upper(U, b):
+    """A x = b with A = U^T U: U^T y = b with k ascending then a division by
+    u_ii, then U x = y with i descending, k = n-1 .. i+1 descending and a
+    division by u_ii (reference trsm Left-Upper-T, then Left-Upper-N)."""
+    b = b[:]
+    n = len(U)
+    for i in range(n):
+        for k in range(i):
+            b[i] = sub(b[i], mul(U[k][i], b[k]))
+        b[i] = div(b[i], U[i][i])
+    for i in range(n - 1, -1, -1):
+        for k in range(n - 1, i, -1):
+            b[i] = sub(b[i], mul(U[i][k], b[k]))
+        b[i] = div(b[i], U[i][i])
+    return b

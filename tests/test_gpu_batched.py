@@ -233,3 +233,28 @@ def test_native_autotune_picks_the_fastest_and_leaves_inputs():
     ps.run(best)
     torch.cuda.synchronize()
     check(ps, host)
+
+
+def test_graph_captured_launch_replays_bit_exact():
+    """The batched launch as it is timed: captured once in a CUDA graph, then
+    replayed twice, each time from the restored inputs; both replays equal
+    the oracle problem by problem (LU, lower and upper Cholesky, 1-3 RHS)."""
+    rng = np.random.default_rng(17)
+    count = 48
+    ns = np.concatenate([[1, 2, 160, 257], rng.integers(3, 130, count - 4)])
+    kinds = np.array([(L, C, CU)[i % 3] for i in range(count)], np.int32)
+    nrhs = rng.integers(1, 4, count)
+    ps, host = make_set(kinds, ns, nrhs, 700)
+    plan = plan_of(256, 2, 96 * 1024)
+    ws = torch.empty(ps.workspace_bytes(plan), dtype=torch.uint8, device="cuda")
+    snap = ps.snapshot()
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    with torch.cuda.graph(g, stream=side):
+        ps.run(plan, ws, stream=side)
+    for rep in range(2):
+        ps.restore(snap)
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        check(ps, host)

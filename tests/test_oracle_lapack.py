@@ -257,6 +257,98 @@ def test_cholesky_and_solve_match_fraction_implementation(n):
     assert x[:, 0].tolist() == fp.rpotrs_lower(F2, b.tolist())
 
 
+def _dirty_words(rng, n):
+    """Random words spread over several binades, so that sums of products
+    round differently in different orders (exact-integer systems cannot see
+    the order)."""
+    return oracle.from_double_array(rng.uniform(-1, 1, size=n) * 2.0 ** rng.integers(-6, 7, size=n))
+
+
+@pytest.mark.parametrize("n", [2, 5, 9])
+def test_lu_transposed_solve_matches_fraction_implementation(n):
+    """O4 with trans = T: U^T forward (k ascending, then divide), unit L^T
+    backward (k ascending), swaps in reverse -- word for word on random
+    words, where the summation order decides the bits."""
+    rng = np.random.default_rng(60 + n)
+    A = rand_words(rng, (n, n))
+    F, ipiv, _ = oracle.rgetrf(A)
+    for rep in range(3):
+        b = _dirty_words(rng, n)
+        x = oracle.rgetrs(F, ipiv, b.reshape(-1, 1), trans="T")
+        assert x[:, 0].tolist() == fp.rgetrs_trans(F.tolist(), list(ipiv), b.tolist())
+
+
+@pytest.mark.parametrize("n", [2, 5, 9])
+def test_upper_cholesky_solve_matches_fraction_implementation(n):
+    """O5 with uplo = U: U^T forward (k ascending, then divide), U backward
+    (k descending, then divide) on the oracle's upper factor."""
+    rng = np.random.default_rng(80 + n)
+    A = _spd_words(rng, n)
+    F, info = oracle.rpotrf(A, uplo="U")
+    assert info == 0
+    for rep in range(3):
+        b = _dirty_words(rng, n)
+        x = oracle.rpotrs(F, b.reshape(-1, 1), uplo="U")
+        assert x[:, 0].tolist() == fp.rpotrs_upper(F.tolist(), b.tolist())
+
+
+def _solve_orders_differ(seed_base, solver, wrong, make):
+    """True when, on one of a few seeded systems, the loop order `wrong`
+    gives other words than `solver`: the pins above can see the order."""
+    for s in range(8):
+        rng = np.random.default_rng(seed_base + s)
+        F, extra, b = make(rng)
+        if solver(F, extra, b) != wrong(F, extra, b):
+            return True
+    return False
+
+
+def test_solve_pins_are_order_sensitive():
+    """The Fraction restatements of the transposed LU solve and the upper
+    Cholesky solve, with one inner loop reversed, give different words on
+    these inputs -- so the word-for-word pins above would fail an oracle
+    with that loop order."""
+    n = 9
+
+    def lu_case(rng):
+        F, ipiv, _ = oracle.rgetrf(rand_words(rng, (n, n)))
+        return F.tolist(), list(ipiv), _dirty_words(rng, n).tolist()
+
+    def lu_wrong(LU, ipiv, b):  # L^T backward with k descending
+        b = b[:]
+        for i in range(n):
+            for k in range(i):
+                b[i] = fp.sub(b[i], fp.mul(LU[k][i], b[k]))
+            b[i] = fp.div(b[i], LU[i][i])
+        for i in range(n - 1, -1, -1):
+            for k in range(n - 1, i, -1):
+                b[i] = fp.sub(b[i], fp.mul(LU[k][i], b[k]))
+        for i in range(n - 1, -1, -1):
+            p = ipiv[i] - 1
+            b[i], b[p] = b[p], b[i]
+        return b
+
+    assert _solve_orders_differ(500, lambda F, p, b: fp.rgetrs_trans(F, p, b), lu_wrong, lu_case)
+
+    def chol_case(rng):
+        F, _ = oracle.rpotrf(_spd_words(rng, n), uplo="U")
+        return F.tolist(), None, _dirty_words(rng, n).tolist()
+
+    def chol_wrong(U, _, b):  # U backward with k ascending
+        b = b[:]
+        for i in range(n):
+            for k in range(i):
+                b[i] = fp.sub(b[i], fp.mul(U[k][i], b[k]))
+            b[i] = fp.div(b[i], U[i][i])
+        for i in range(n - 1, -1, -1):
+            for k in range(i + 1, n):
+                b[i] = fp.sub(b[i], fp.mul(U[i][k], b[k]))
+            b[i] = fp.div(b[i], U[i][i])
+        return b
+
+    assert _solve_orders_differ(600, lambda F, _, b: fp.rpotrs_upper(F, b), chol_wrong, chol_case)
+
+
 def test_nar_pivot_propagates():
     """G8: NaR compares as the largest |a| and is chosen as pivot."""
     rng = np.random.default_rng(5)

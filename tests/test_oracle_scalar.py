@@ -133,6 +133,35 @@ def test_exhaustive_posit16(posit_checker, op):
     assert bad == 0, out
 
 
+@pytest.mark.parametrize("op", ["add", "sub", "mul", "div"])
+def test_posit16_slice_exhaustive(posit_checker, op):
+    """P4 in the default run: Posit(16,2), every second operand against the
+    first operands a = 37 (mod 64) -- 2^26 pairs per operation, a fixed 1/64
+    slice of the full all-pairs run (recorded in tests/golden/
+    posit16_exhaustive.txt: 0 failures in 2^32 pairs per operation)."""
+    checked, bad, out = posit_checker("exhaustive", 16, op, 64, 37)
+    assert checked == (1 << 26) and bad == 0, out
+
+
+def test_posit16_full_run_record():
+    """The recorded full Posit(16,2) run covers every operation with every
+    pair and reports no failure."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "posit16_exhaustive.txt")
+    rows = {}
+    with open(path) as f:
+        for ln in f:
+            if ln.startswith("#") or not ln.strip():
+                continue
+            op, *kv = ln.split()
+            rows[op] = dict(p.split("=") for p in kv)
+    for op in ("add", "sub", "mul", "div"):
+        assert int(rows[op]["checked"]) == 1 << 32 and int(rows[op]["bad"]) == 0
+    for op in ("sqrt", "recip"):
+        assert int(rows[op]["checked"]) == 1 << 16 and int(rows[op]["bad"]) == 0
+
+
 @pytest.mark.parametrize("op", ["add", "mul", "div"])
 def test_posit16_sampled(op):
     """P4 in the default run: Posit(16,2) all a against a stride of b, checked
