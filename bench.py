@@ -50,6 +50,13 @@ FMA_INST_PER_MAC = 0.8069  # sm__inst_executed_pipe_fmaheavy.sum: 4.43614e11 / 5
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one captured
 # 8192^3 launch.
 TRAFFIC_8192 = 4.99843e9 + 0.42177e9
+# The counters above belong to one build of the kernel: the SHA-256 (first 16
+# hex digits) of the two source files that define it when they were taken.
+# If the sources differ, the line says "counters_stale": true, its traffic is
+# null, and the achieved figures are estimates from the old counts.
+COUNTERS_SOURCES = ("paper_2401_14117_gb300/csrc/rgemm.cu",
+                    "paper_2401_14117_gb300/csrc/posit_core.cuh")
+COUNTERS_SOURCE_SHA = "7bf192eccc3d28cf"
 # The kernel is bound by the integer ALU pipe: 16 lanes per scheduler, i.e.
 # 0.5 warp instruction per clock per scheduler (the rate at which ncu's
 # sm__inst_executed_pipe_alu.avg.pct_of_peak_sustained_active reads 100 %).
@@ -58,12 +65,23 @@ SM_COUNT = 152
 SCHEDULERS_PER_SM = 4
 
 
+def kernel_source_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in COUNTERS_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--probe", action="store_true",
+                   help="run the dependency-free issue probe instead of the benchmark")
     p.add_argument("--size", type=int, default=8192, help="M = N = K")
     p.add_argument("--k", type=int, default=None, help="override K (e.g. 256)")
     p.add_argument("--no-e2e", action="store_true")
@@ -74,9 +92,16 @@ def parse():
     p.add_argument("--serve-seconds", type=float, default=10.0)
     p.add_argument("--serve-rate-sustained", type=float, default=60.0,
                    help="arrival rate (requests/s) of the sustainable serving run")
+    p.add_argument("--serve-pool", type=int, default=96,
+                   help="seeded problems in the serving pool")
+    p.add_argument("--serve-rates", default="40,80,120,160,240,320,480",
+                   help="arrival rates of the serving_sweep section")
+    p.add_argument("--serve-slo-ms", type=float, default=250.0,
+                   help="p99 latency objective of the serving_sweep section")
     p.add_argument("--extras", default="all",
                    help="comma list of extra workloads: elementwise, rgemm, ksweep, sigma, "
-                        "factor, power, accuracy, batched, serving; or all")
+                        "factor, power, accuracy, batched, serving; or all (serving_sweep, "
+                        "the arrival-rate sweep, only when named)")
     p.add_argument("--ew-size", type=int, default=1 << 24,
                    help="elements per element-wise launch")
     return p.parse_args()
@@ -369,9 +394,13 @@ def run_ours(args):
     # issue slots, for context: 1 warp instruction per clock per scheduler
     issue_peak = SM_COUNT * SCHEDULERS_PER_SM * peak_clock * 1e6 / 1e9
     issue = INST_PER_MAC * macs / launch_s / 1e9
-    traffic = TRAFFIC_8192 if (m, n, k) == (8192, 8192, 8192) else None
+    stale = kernel_source_sha() != COUNTERS_SOURCE_SHA
+    traffic = TRAFFIC_8192 if (m, n, k) == (8192, 8192, 8192) and not stale else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "G ALU-pipe warp-inst/s", "frac": achieved / peak,
+                "counters_stale": stale, "counters_source_sha": COUNTERS_SOURCE_SHA,
+                # 32 threads per warp instruction, 2 posit ops per multiply-add
+                "thread_inst_per_posit_op": INST_PER_MAC * 32 / 2,
                 "traffic": traffic, "traffic_unit": "bytes per launch",
                 "algorithmic_bytes": 4.0 * (m * k + k * n + m * n),
                 "kernel": "rgemm_kernel<false,false,0,4>", "launch_ms": launch_ms,
@@ -401,6 +430,89 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ probe
+# A dependency-free issue probe: eight independent chains per thread of one
+# instruction kind, no memory traffic in the loop.  It measures the ceilings
+# the Rgemm roofline is quoted against: LOP3 only (the integer ALU pipe),
+# IMAD only (the FMA-heavy pipe, which runs integer multiply-adds), and the
+# two interleaved 1:1 (the issue slot).  Run it under ncu with the pipe
+# counters to see where each kind executes.
+PROBE_SRC = r"""
+#define CHAINS(OP) OP(a0) OP(a1) OP(a2) OP(a3) OP(a4) OP(a5) OP(a6) OP(a7)
+#define LOP(a) asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(a) : "r"(c1), "r"(c2));
+#define MAD(a) asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a) : "r"(c1), "r"(c2));
+template <int KIND>
+__global__ void probe(unsigned *out, int iters, unsigned c1, unsigned c2) {
+  unsigned a0 = threadIdx.x, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3;
+  unsigned a4 = a0 + 4, a5 = a0 + 5, a6 = a0 + 6, a7 = a0 + 7;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (KIND == 0) { CHAINS(LOP) CHAINS(LOP) }
+      if (KIND == 1) { CHAINS(MAD) CHAINS(MAD) }
+      if (KIND == 2) { CHAINS(LOP) CHAINS(MAD) }
+    }
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = a0 ^ a1 ^ a2 ^ a3 ^ a4 ^ a5 ^ a6 ^ a7;
+}
+extern "C" int run_probe(int kind, int blocks, int threads, int iters, float *ms) {
+  unsigned *out;
+  if (cudaMalloc(&out, sizeof(unsigned) * blocks * threads) != cudaSuccess) return 1;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int rep = 0; rep < 2; ++rep) {
+    cudaEventRecord(e0);
+    if (kind == 0) probe<0><<<blocks, threads>>>(out, iters, 0x9E3779B9u, 0x7F4A7C15u);
+    if (kind == 1) probe<1><<<blocks, threads>>>(out, iters, 0x9E3779B9u, 0x7F4A7C15u);
+    if (kind == 2) probe<2><<<blocks, threads>>>(out, iters, 0x9E3779B9u, 0x7F4A7C15u);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+  }
+  cudaEventElapsedTime(ms, e0, e1);
+  cudaFree(out);
+  return cudaGetLastError() != cudaSuccess;
+}
+"""
+
+
+def run_probe(args):
+    """Compile and run the issue probe; prints one JSON line per kind with
+    the warp instructions of the unrolled body (16 per inner step) per clock
+    per scheduler at the sampled SM clock."""
+    import ctypes
+    import tempfile
+
+    import torch
+    torch.cuda.init()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "probe.cu")
+        lib = os.path.join(d, "probe.so")
+        with open(src, "w") as f:
+            f.write(PROBE_SRC)
+        from paper_2401_14117_gb300 import build as pbuild
+        subprocess.run([pbuild._nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-O3",
+                        "-Xcompiler", "-fPIC", "-shared", "-o", lib, src], check=True)
+        L = ctypes.CDLL(lib)
+        blocks, threads, iters = sms * 4, 512, 1 << 18  # about 0.25 s per launch
+        for kind, name in ((0, "lop3 (ALU pipe)"), (1, "imad (FMA-heavy pipe)"),
+                           (2, "lop3 + imad 1:1")):
+            ms = ctypes.c_float()
+            with ClockSampler(0) as clk:
+                rc = L.run_probe(kind, blocks, threads, iters, ctypes.byref(ms))
+            if rc:
+                raise RuntimeError("probe launch failed")
+            clocks = clk.summary()
+            mhz = clocks.get("sm_mhz") or 2070.0
+            warp_inst = blocks * threads / 32 * iters * 8 * 16
+            per_clk = warp_inst / (ms.value / 1e3 * mhz * 1e6) / (sms * 4)
+            print(json.dumps({"probe": name, "ms": ms.value, "sm_mhz": mhz,
+                              "warp_inst_per_clk_per_scheduler": per_clk,
+                              "counted": "16 per inner step (loop overhead excluded)",
+                              "clocks": clocks}), flush=True)
 
 
 # ------------------------------------------------------------------ extras
@@ -687,12 +799,13 @@ def extras(args, dev, stream):
         out["batched"] = batched
 
     # serving: Poisson 2000 req/s, n log-uniform [64, 4096], nrhs 1..8
+    servers = (("continuous_batching", 512), ("per_request_plain", 1))
     if want("serving"):
         serve = {}
         for chol, label in ((binding.POSIT_CHOLESKY_U, "cholesky_U"), (binding.POSIT_CHOLESKY, "cholesky_L")):
-            pool = serving.Pool(96, 64, 4096, 8, seed=20240129, cholesky_kind=chol)
+            pool = serving.Pool(args.serve_pool, 64, 4096, 8, seed=20240129, cholesky_kind=chol)
             t, idx = serving.arrivals(2000.0, args.serve_seconds, pool.size, seed=7)
-            for name, small in (("continuous_batching", 512), ("per_request_plain", 1)):
+            for name, small in servers:
                 cfg = serving.default_config(budget_gb=40.0, small_n_max=small)
                 r = serving.run(pool, t, idx, cfg, duration=args.serve_seconds, max_outstanding=256)
                 r.pop("kept")
@@ -701,7 +814,7 @@ def extras(args, dev, stream):
                 # a rate the server sustains (offered work below its capacity)
                 rate = args.serve_rate_sustained
                 t2, idx2 = serving.arrivals(rate, args.serve_seconds, pool.size, seed=8)
-                for name, small in (("continuous_batching", 512), ("per_request_plain", 1)):
+                for name, small in servers:
                     cfg = serving.default_config(budget_gb=40.0, small_n_max=small)
                     r = serving.run(pool, t2, idx2, cfg, duration=args.serve_seconds,
                                     max_outstanding=256)
@@ -710,16 +823,43 @@ def extras(args, dev, stream):
             del pool
         serve["workload"] = (f"Poisson 2000/s (and {args.serve_rate_sustained:g}/s), n log-uniform "
                              f"[64, 4096], nrhs 1-8, LU/Cholesky 50/50, {args.serve_seconds:.0f} s, "
-                             "40 GB budget, pool of 96 seeded problems; latency from arrival "
-                             "(queueing included)")
+                             f"40 GB budget, pool of {args.serve_pool} seeded problems; latency "
+                             "from arrival (queueing included), p50/p99 over every offered "
+                             "request (unfinished ones censored at the end of the run)")
         out["serving"] = serve
+
+    # arrival-rate sweep of both servers: the highest rate each holds with
+    # p99 under the SLO (requested explicitly: --extras serving_sweep)
+    if "serving_sweep" in sections:
+        slo = args.serve_slo_ms
+        pool = serving.Pool(args.serve_pool, 64, 4096, 8, seed=20240129,
+                            cholesky_kind=binding.POSIT_CHOLESKY_U)
+        sweep = {"slo_ms": slo, "seconds_per_rate": args.serve_seconds, "pool": args.serve_pool,
+                 "rates": [float(x) for x in args.serve_rates.split(",")]}
+        for name, small in servers:
+            rows, best = [], None
+            for rate in sweep["rates"]:
+                t, idx = serving.arrivals(rate, args.serve_seconds, pool.size, seed=11)
+                cfg = serving.default_config(budget_gb=40.0, small_n_max=small)
+                r = serving.run(pool, t, idx, cfg, duration=args.serve_seconds,
+                                max_outstanding=1024)
+                r.pop("kept")
+                r["rate"] = rate
+                rows.append(r)
+                if r["p99_ms"] is not None and r["p99_ms"] <= slo and r["censored"] == 0:
+                    best = rate
+            sweep[name] = {"runs": rows, "highest_rate_within_slo": best}
+        del pool
+        out["serving_sweep"] = sweep
 
     return out
 
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.probe:
+        run_probe(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -273,7 +273,12 @@ POSIT_API int posit_autotune(int64_t count, const posit_problem *problems, const
  * max_batch) goes into one persistent posit_factor_solve_batched launch with
  * `plan`.  Larger requests run through the blocked multi-SM routines, up to
  * large_lanes of them at once on their own streams, concurrently with the
- * small lane.  X receives
+ * small lane.  Latency first: while a large lane is idle and no large
+ * request waits, a waiting small request with n > batch_only_n_max takes
+ * that lane (the multi-SM routines finish it sooner than one CTA of a
+ * batch); under load the lanes are busy and such requests are batched
+ * (batch_only_n_max >= small_n_max: every small request is batched).
+ * X receives
  * the solution (LU: posit_rgetrs 'N'; Cholesky: posit_rpotrs 'L' or, for
  * POSIT_CHOLESKY_U, 'U' -- or B unchanged if the factorisation failed) and
  * *info the factorisation's info,
@@ -292,6 +297,9 @@ typedef struct posit_serve_config {
   int32_t max_nrhs;      /* largest nrhs accepted */
   int32_t large_lanes;   /* concurrent large requests (streams); 0 means 16 */
   posit_plan plan;       /* batched launch shape */
+  int32_t batch_only_n_max; /* small requests with n above this take an idle
+                               large lane instead of waiting for a batch */
+  int32_t reserved;
 } posit_serve_config;
 
 typedef struct posit_request {

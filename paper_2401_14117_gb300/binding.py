@@ -62,7 +62,8 @@ class posit_plan(ctypes.Structure):
 class posit_serve_config(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_int64), ("small_n_max", ctypes.c_int32),
                 ("max_batch", ctypes.c_int32), ("max_nrhs", ctypes.c_int32),
-                ("large_lanes", ctypes.c_int32), ("plan", posit_plan)]
+                ("large_lanes", ctypes.c_int32), ("plan", posit_plan),
+                ("batch_only_n_max", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class posit_request(ctypes.Structure):

@@ -52,16 +52,19 @@ int potrf_run(bool upper, int64_t n, uint32_t *A, int64_t lda, int32_t *info, vo
 // created on first use, kept for the life of the process); nullptr on error.
 cudaStream_t lookahead_stream();
 
-// Solves on a caller-provided scratch block of solve_scratch_bytes() bytes.
-size_t solve_scratch_bytes();
+// Solves on a caller-provided scratch block of scratch_bytes bytes (device
+// memory); solve_scratch_bytes(n) is enough for any nrhs (smaller blocks
+// solve fewer right-hand sides per launch, at least 8 n / 32 + 264 bytes).
+size_t solve_scratch_bytes(int64_t n);
 int getrs_run(bool trans, int64_t n, int64_t nrhs, const uint32_t *A, int64_t lda,
-              const int32_t *ipiv, uint32_t *B, int64_t ldb, void *scratch, cudaStream_t stream);
+              const int32_t *ipiv, uint32_t *B, int64_t ldb, void *scratch, size_t scratch_bytes,
+              cudaStream_t stream);
 int potrs_run(bool upper, int64_t n, int64_t nrhs, const uint32_t *A, int64_t lda, uint32_t *B,
-              int64_t ldb, void *scratch, cudaStream_t stream);
+              int64_t ldb, void *scratch, size_t scratch_bytes, cudaStream_t stream);
 // Same, skipped on the device when *abort_flag != 0 (a failed factorisation).
 int potrs_run_guarded(bool upper, int64_t n, int64_t nrhs, const uint32_t *A, int64_t lda,
                       uint32_t *B, int64_t ldb, const int32_t *abort_flag, void *scratch,
-                      cudaStream_t stream);
+                      size_t scratch_bytes, cudaStream_t stream);
 
 // Batched factor + solve (batched.cu).
 size_t batched_workspace_bytes(int max_n, int max_nrhs, const posit_plan &plan);

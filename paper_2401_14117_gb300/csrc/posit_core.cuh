@@ -539,8 +539,9 @@ static __device__ __forceinline__ uint32_t pz_sig_sqrt(uint64_t N, uint32_t &ine
 }
 
 // a (/) b, one rounding: 32 quotient bits of the significands plus the
-// inexact (jam) bit.
-static __device__ __noinline__ pz pz_div(pz a, pz b) {
+// inexact (jam) bit.  pz_div_inline for straight-line code that overlaps the
+// division with other work; pz_div keeps it out of line elsewhere.
+static __device__ __forceinline__ pz pz_div_inline(pz a, pz b) {
   if (pz_is_nar(a) || pz_is_nar(b) || pz_is_zero(b)) return pz_nar();
   if (pz_is_zero(a)) return pz_zero();
   uint32_t A = a.m & 0x7FFFFFFFu, B = b.m & 0x7FFFFFFFu;  // both in [2^30, 2^31)
@@ -556,6 +557,8 @@ static __device__ __noinline__ pz pz_div(pz a, pz b) {
   }
   return pz_round((a.m ^ b.m) & 0x80000000u, S, X);
 }
+
+static __device__ __noinline__ pz pz_div(pz a, pz b) { return pz_div_inline(a, b); }
 
 // sqrt(a), one rounding: the integer square root of the significand scaled
 // to 64 bits, plus the inexact (jam) bit.

@@ -57,6 +57,7 @@ struct posit_server {
   std::vector<posit::Launch> inflight;
   bool small_busy = false;
   size_t used = 0;
+  size_t lane_scratch = 0;  // bytes of each large lane's scratch
   void *ws = nullptr;  // batched workspace (small lane)
   posit_problem *stage = nullptr;  // pinned staging for descriptors
   int64_t stage_cap = 0;
@@ -161,12 +162,16 @@ int start_large(posit_server *sv, int lane, cudaEvent_t ready) {
   const int64_t n = q.r.n, k = q.r.nrhs;
   if (q.r.kind == POSIT_LU) {
     st = getrf_run(n, n, q.dA, n, q.dipiv, q.dinfo, ln.scratch, ln.stream);
-    if (!st) st = getrs_run(false, n, k, q.dA, n, q.dipiv, q.dB, n, ln.scratch, ln.stream);
+    if (!st)
+      st = getrs_run(false, n, k, q.dA, n, q.dipiv, q.dB, n, ln.scratch, sv->lane_scratch,
+                     ln.stream);
   } else {
     const bool upper = q.r.kind == POSIT_CHOLESKY_U;
     st = potrf_run(upper, n, q.dA, n, q.dinfo, ln.scratch, ln.stream);
     // the solve is skipped on the device when info != 0 (B then keeps b)
-    if (!st) st = potrs_run_guarded(upper, n, k, q.dA, n, q.dB, n, q.dinfo, ln.scratch, ln.stream);
+    if (!st)
+      st = potrs_run_guarded(upper, n, k, q.dA, n, q.dB, n, q.dinfo, ln.scratch,
+                             sv->lane_scratch, ln.stream);
   }
   if (st) return st;
   if ((st = finish_copies(sv, q, ln.stream))) return st;
@@ -192,7 +197,8 @@ extern "C" int posit_serve_open(const posit_serve_config *cfg, posit_server **ou
   if (!cfg) return -1;
   if (!out) return -2;
   if (cfg->budget_bytes <= 0 || cfg->small_n_max < 1 || cfg->small_n_max > 46340 ||
-      cfg->max_batch < 1 || cfg->max_nrhs < 1 || cfg->large_lanes < 0 || cfg->large_lanes > 64)
+      cfg->max_batch < 1 || cfg->max_nrhs < 1 || cfg->large_lanes < 0 || cfg->large_lanes > 64 ||
+      cfg->batch_only_n_max < 0)
     return -1;
   posit_server *sv = new (std::nothrow) posit_server();
   if (!sv) return POSIT_ERR_ALLOC;
@@ -203,7 +209,9 @@ extern "C" int posit_serve_open(const posit_serve_config *cfg, posit_server **ou
       cudaStreamCreateWithFlags(&sv->s_copy, cudaStreamNonBlocking) != cudaSuccess)
     st = POSIT_ERR_CUDA;
   size_t wsb = batched_workspace_bytes(cfg->small_n_max, cfg->max_nrhs, cfg->plan);
-  size_t scr = std::max(getrf_scratch_bytes(), solve_scratch_bytes());
+  // solves of any n fit (fewer right-hand sides per launch past n = 2^20)
+  size_t scr = std::max(getrf_scratch_bytes(), solve_scratch_bytes(1 << 20));
+  sv->lane_scratch = scr;
   if (!st && (!wsb || cudaMalloc(&sv->ws, wsb) != cudaSuccess)) st = POSIT_ERR_ALLOC;
   sv->lanes.resize(sv->cfg.large_lanes);
   for (auto &ln : sv->lanes) {
@@ -290,10 +298,24 @@ extern "C" int posit_serve_poll(posit_server *sv, uint64_t *done_tags, int64_t m
   }
   // 3. start launches on idle lanes; they wait for the admitted copies
   (void)any;
+  int idle = 0;
+  for (auto &ln : sv->lanes) idle += !ln.busy;
+  // latency first: idle large lanes left over after the large requests take
+  // the waiting small requests that are too big to be quick in one CTA
+  {
+    int spare = idle - (int)sv->large_ready.size();
+    for (auto it = sv->small_ready.begin(); spare > 0 && it != sv->small_ready.end();) {
+      if (sv->reqs[*it].r.n > sv->cfg.batch_only_n_max) {
+        sv->large_ready.push_back(*it);
+        it = sv->small_ready.erase(it);
+        --spare;
+      } else {
+        ++it;
+      }
+    }
+  }
   bool small_go = !sv->small_busy && !sv->small_ready.empty();
-  bool large_go = false;
-  for (auto &ln : sv->lanes) large_go |= !ln.busy;
-  large_go &= !sv->large_ready.empty();
+  bool large_go = idle > 0 && !sv->large_ready.empty();
   if (small_go || large_go) {
     cudaEvent_t ready = nullptr;
     if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess ||

@@ -7,6 +7,8 @@ a request is handed to the server once its arrival time has passed and fewer
 than `max_outstanding` requests are inside the server; the latency of a
 request is measured from its arrival time, so waiting in the client queue is
 part of it (reported separately from the time spent inside the server).
+p50/p99 cover every request offered in the window; one not finished when the
+run ends counts with its wait so far (censored, a lower bound).
 All matrix data is produced and converted on the GPU (the library's
 conversion kernel); this module only moves buffers and keeps time.
 """
@@ -62,9 +64,12 @@ class Pool:
 
 
 def default_config(budget_gb=40.0, small_n_max=512, max_batch=1024, max_nrhs=8,
-                   plan=(256, 4, 48 * 1024), large_lanes=16):
+                   plan=(256, 4, 48 * 1024), large_lanes=16, batch_only_n_max=128):
+    """batch_only_n_max: small requests above it take an idle large lane
+    (latency first); at or above small_n_max every small request is batched."""
     return binding.posit_serve_config(int(budget_gb * 2 ** 30), small_n_max, max_batch,
-                                      max_nrhs, large_lanes, binding.posit_plan(*plan, 0))
+                                      max_nrhs, large_lanes, binding.posit_plan(*plan, 0),
+                                      batch_only_n_max, 0)
 
 
 def run(pool, arrival_times, pool_index, cfg, duration, max_outstanding=256, capture=None,
@@ -127,16 +132,33 @@ def run(pool, arrival_times, pool_index, cfg, duration, max_outstanding=256, cap
     completed = ~np.isnan(done_t)
     lat = (done_t - arrival)[completed]
     svc = (done_t - submit_t)[completed]
+    # every request offered in the window: one still waiting (in the client
+    # queue or in the server) when the run ends counts with its wait so far,
+    # a lower bound of its latency (censored)
+    censored = in_window & ~completed
+    lat_all = np.where(completed, done_t - arrival, elapsed - arrival)[in_window]
     ops = sum(pool.ops(int(pool_index[r])) for r in np.flatnonzero(completed))
+
+    def pct(v, q):
+        return float(np.percentile(v, q) * 1e3) if v.size else None
+
+    p99_all = pct(lat_all, 99)
     return {
         "offered": int(in_window.sum()),
         "submitted": int(nxt),
         "completed": int(completed.sum()),
+        "censored": int(censored.sum()),
         "elapsed_s": elapsed,
         "solves_per_s": float(completed.sum()) / min(elapsed, duration if not drain else elapsed),
         "goodput_gflops": ops / elapsed / 1e9,
-        "p50_ms": float(np.percentile(lat, 50) * 1e3) if lat.size else None,
-        "p99_ms": float(np.percentile(lat, 99) * 1e3) if lat.size else None,
+        # over every offered request, the censored ones at their wait so far
+        "p50_ms": pct(lat_all, 50),
+        "p99_ms": p99_all,
+        "p99_is_lower_bound": bool(censored.sum() > 0 and lat_all.size
+                                   and (elapsed - arrival[censored]).max() * 1e3 >= p99_all),
+        # over the completed requests only
+        "completed_p50_ms": pct(lat, 50),
+        "completed_p99_ms": pct(lat, 99),
         "service_p50_ms": float(np.percentile(svc, 50) * 1e3) if svc.size else None,
         "service_p99_ms": float(np.percentile(svc, 99) * 1e3) if svc.size else None,
         "launches": int(stats.launches),

@@ -154,6 +154,50 @@ def test_getrf_workload_8192_sampled():
         assert int(vals[0]) == int(F[k, k])
 
 
+def _factor_record(tag):
+    """The oracle's n = 8192 factorisation record for `tag` (lu / chol):
+    digests, info and per-column CRC-32s (tests/golden/factor8192.txt)."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "factor8192.txt")
+    rec, crcs = {}, {}
+    with open(path) as f:
+        for ln in f:
+            if ln.startswith("#") or not ln.strip():
+                continue
+            t, key, *rest = ln.split()
+            if t != tag:
+                continue
+            if key == "crc32":
+                c0 = int(rest[0])
+                for q, h in enumerate(rest[1:]):
+                    crcs[c0 + q] = int(h, 16)
+            else:
+                rec[key] = rest[0]
+    return rec, crcs
+
+
+@pytest.mark.parametrize("kind", ["lu", "chol"])
+def test_factor_8192_full_against_oracle_record(kind):
+    """n = 8192, every word: the GPU factors, pivots and info against the CPU
+    oracle's unblocked factorisation of the same matrix (Sec. 5.2), stored as
+    digests by tests/golden/make_factor8192.py; on a mismatch the first
+    differing column is located through the per-column CRC-32s."""
+    from tests.golden import make_factor8192 as mf
+    rec, crcs = _factor_record(kind)
+    A = mf.lu_input() if kind == "lu" else mf.chol_input()
+    assert mf.sha(A) == rec["input_sha256"], "the regenerated input is not the recorded one"
+    if kind == "lu":
+        F, ipiv, info = gpu_getrf(A)
+        assert mf.sha(ipiv.astype(np.int32)) == rec["ipiv_sha256"], "pivots differ"
+    else:
+        F, info = gpu_potrf(A, "L")
+    assert info == int(rec["info"])
+    if mf.sha(F) != rec["factor_sha256"]:
+        got = mf.column_crcs(F)
+        bad = [j for j in range(len(got)) if got[j] != crcs[j]]
+        pytest.fail(f"{kind} 8192: {len(bad)} columns differ from the oracle, first {bad[:5]}")
+
+
 # ----------------------------------------------------------------- Rpotrf
 @pytest.mark.parametrize("n", [1, 5, 64, 255, 300, 513, 700])
 @pytest.mark.parametrize("uplo", ["L", "U"])
@@ -360,3 +404,42 @@ def test_argument_errors():
     binding.posit_rgetrf(0, 5, None, 1, None, info)
     binding.posit_rpotrf("L", 0, None, 1, info)
     assert int(info.item()) == 0
+
+
+@pytest.mark.parametrize("case", ["tiny_pivots", "huge_entries", "nar_entry", "in_band"])
+@pytest.mark.parametrize("kind", ["getrs_N", "getrs_T", "potrs_L", "potrs_U"])
+def test_solve_fast_path_switches(case, kind):
+    """The wavefront solves run on in-band straight-line arithmetic while the
+    tiles, the unknowns and the running sums allow it, and switch to the
+    general arithmetic where they do not: a pivot of 2^-45 mid-block makes an
+    unknown leave the band (the step is redone), entries of 2^50 make a tile
+    leave it, a NaR entry poisons the rows below it.  Every case must give the
+    oracle's words, on factor-shaped matrices of 300 rows (10 blocks, ragged
+    tail) with 2 right-hand sides."""
+    n, nrhs = 300, 2
+    rng = np.random.default_rng(4242 + len(case) + len(kind))
+    F = words((n, n), 777 + len(case))
+    d = np.arange(n)
+    F[d, d] = oracle.from_double_array(rng.uniform(1.0, 2.0, n))
+    if case == "tiny_pivots":
+        for i in (37, 70, 203, 299):
+            F[i, i] = oracle.from_double(2.0 ** -45)
+    elif case == "huge_entries":
+        for (i, k) in ((150, 20), (20, 150), (260, 100), (100, 260)):
+            F[i, k] = oracle.from_double(2.0 ** 50)
+    elif case == "nar_entry":
+        F[180, 60] = 0x80000000
+        F[60, 180] = 0x80000000
+    B = words((n, nrhs), 901 + len(kind))
+    dF, dB = to_dev(F), to_dev(B)
+    if kind.startswith("getrs"):
+        trans = kind[-1]
+        ipiv = (d + rng.integers(0, 8, n)).clip(max=n - 1).astype(np.int32) + 1
+        want = oracle.rgetrs(F, ipiv, B, trans=trans)
+        binding.posit_rgetrs(trans, n, nrhs, dF, n, torch.from_numpy(ipiv).to(DEV), dB, n)
+    else:
+        uplo = kind[-1]
+        want = oracle.rpotrs(F, B, uplo=uplo)
+        binding.posit_rpotrs(uplo, n, nrhs, dF, n, dB, n)
+    torch.cuda.synchronize()
+    assert_same(from_dev(dB), want, f"{kind} {case}")

@@ -1,6 +1,9 @@
 """The continuous-batching server: every served result equals the result of
 the same problem solved alone (single-problem routines) -- and, for the
 smaller problems, the CPU oracle -- whatever else was in flight."""
+import ctypes
+import time
+
 import numpy as np
 import pytest
 import torch
@@ -92,3 +95,45 @@ def test_budget_too_small_for_a_request_is_rejected():
         assert e.value.code == -2
     finally:
         binding.posit_serve_close(server)
+
+
+def test_budget_defers_admission_and_results_stay_exact():
+    """Admission by device-memory budget under load: twelve requests are
+    submitted at once to a server whose budget holds two of them, so the
+    others wait in `pending` (never more than the budget in use) and are
+    admitted as memory frees up; every result still equals the problem solved
+    alone, and the CPU oracle."""
+    pool = serving.Pool(12, 200, 260, 2, seed=91, cholesky_kind=binding.POSIT_CHOLESKY_U)
+    sizes = [int(pool.ns[i]) ** 2 * 4 + int(pool.ns[i]) * 16 + 1024 for i in range(pool.size)]
+    budget = int(2.2 * max(sizes))
+    cfg = serving.default_config(budget_gb=budget / 2 ** 30, small_n_max=512, max_batch=64)
+    server = binding.posit_serve_open(cfg)
+    X = [torch.zeros(int(pool.ns[i] * pool.nrhs[i]), dtype=torch.int32, pin_memory=True)
+         for i in range(pool.size)]
+    INFO = torch.zeros(pool.size, dtype=torch.int32, pin_memory=True)
+    done, max_pending, max_used = set(), 0, 0
+    tags = (ctypes.c_uint64 * pool.size)()
+    try:
+        for i in range(pool.size):
+            binding.posit_serve_submit(server, binding.posit_request(
+                int(pool.kinds[i]), int(pool.ns[i]), int(pool.nrhs[i]), 0, pool.A[i].data_ptr(),
+                pool.B[i].data_ptr(), X[i].data_ptr(), INFO.data_ptr() + 4 * i, i))
+        t0 = time.perf_counter()
+        while len(done) < pool.size and time.perf_counter() - t0 < 60:
+            got = binding.posit_serve_poll(server, tags, pool.size)
+            st = binding.posit_serve_stats(server)
+            max_pending = max(max_pending, int(st.pending))
+            max_used = max(max_used, int(st.device_bytes_in_use))
+            done.update(int(tags[k]) for k in range(got))
+            time.sleep(50e-6)
+    finally:
+        binding.posit_serve_close(server)
+    assert len(done) == pool.size
+    assert max_pending >= pool.size - 3  # the budget, not a slot limit, held them back
+    assert 0 < max_used <= budget
+    for i in range(pool.size):
+        x = X[i].numpy().view(np.uint32)
+        ax, ainfo = alone(pool, i)
+        assert int(INFO[i]) == ainfo and np.array_equal(x, ax), i
+        ox, oinfo = oracle_solution(pool, i)
+        assert oinfo == ainfo and np.array_equal(ax, ox), i
