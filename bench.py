@@ -40,26 +40,26 @@ UNIT = "Gflops"
 ONE = 0x40000000
 
 # Per posit multiply-add of the rgemm kernel, from one ncu capture of one
-# launch of the current kernel (NN, uniform [-1,1]; the counts are set by the
-# inner loop, so they scale with M N K): integer-ALU-pipe warp instructions
-# (sm__inst_executed_pipe_alu.sum / M N K) and all warp instructions
-# (smsp__inst_executed.sum / M N K).
-ALU_INST_PER_MAC = 1.0648  # 5.85386e11 / 5.49756e11 (NN 8192^3)
-INST_PER_MAC = 2.0067      # 1.10319e12 / 5.49756e11
-FMA_INST_PER_MAC = 0.8069  # sm__inst_executed_pipe_fmaheavy.sum: 4.43614e11 / 5.49756e11
+# 4096^3 launch of the current kernel (NN, uniform [-1,1]; the counts are set
+# by the inner loop, so they scale with M N K): integer-ALU-pipe warp
+# instructions (sm__inst_executed_pipe_alu.sum / M N K), all warp
+# instructions (smsp__inst_executed.sum / M N K) and FMA-heavy-pipe ones.
+ALU_INST_PER_MAC = 1.06493  # 7.31809e10 / 6.87195e10 (NN 4096^3)
+INST_PER_MAC = 2.00693      # 1.37914e11 / 6.87195e10
+FMA_INST_PER_MAC = 0.80698  # sm__inst_executed_pipe_fmaheavy.sum: 5.54547e10 / 6.87195e10
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one captured
-# 8192^3 launch.
-TRAFFIC_8192 = 4.99843e9 + 0.42177e9
+# 8192^3 launch (one-pass capture of the full-size workload).
+TRAFFIC_8192 = 4.972963e9 + 0.419838e9
 # The counters above belong to one build of the kernel: the SHA-256 (first 16
 # hex digits) of the two source files that define it when they were taken.
 # If the sources differ, the line says "counters_stale": true, its traffic is
 # null, and the achieved figures are estimates from the old counts.
 COUNTERS_SOURCES = ("paper_2401_14117_gb300/csrc/rgemm.cu",
                     "paper_2401_14117_gb300/csrc/posit_core.cuh")
-COUNTERS_SOURCE_SHA = "7bf192eccc3d28cf"
-# The kernel is bound by the integer ALU pipe: 16 lanes per scheduler, i.e.
-# 0.5 warp instruction per clock per scheduler (the rate at which ncu's
-# sm__inst_executed_pipe_alu.avg.pct_of_peak_sustained_active reads 100 %).
+COUNTERS_SOURCE_SHA = "118032ce3e53eee9"
+# The kernel is bound by the integer ALU pipe: 0.5 warp instruction per clock
+# per scheduler, measured by the issue probe (python bench.py --probe under
+# ncu): LOP3 chains alone, all on the ALU pipe, run at 0.4993.
 ALU_WARP_INST_PER_CLK = 0.5
 SM_COUNT = 152
 SCHEDULERS_PER_SM = 4
@@ -92,6 +92,10 @@ def parse():
     p.add_argument("--serve-seconds", type=float, default=10.0)
     p.add_argument("--serve-rate-sustained", type=float, default=60.0,
                    help="arrival rate (requests/s) of the sustainable serving run")
+    p.add_argument("--batch-count", type=int, default=4096,
+                   help="problems in the batched section")
+    p.add_argument("--batch-plan", default="",
+                   help="threads,ctas_per_sm,smem_bytes for the batched section (default: autotuned)")
     p.add_argument("--serve-pool", type=int, default=96,
                    help="seeded problems in the serving pool")
     p.add_argument("--serve-rates", default="40,80,120,160,240,320,480",
@@ -702,7 +706,15 @@ def extras(args, dev, stream):
         b = torch.empty_like(b0)
         ms = _time_ms(lambda: binding.posit_rgetrs("N", n, 1, A, n, ipiv, b, n, stream), stream,
                       setup=lambda: b.copy_(b0))
-        fac["rgetrs_8192"] = {"ms": ms, "GB/s (factor read once)": 4.0 * n * n / (ms / 1e3) / 1e9}
+        fac["rgetrs_8192"] = {"ms": ms, "GB/s (factor read once)": 4.0 * n * n / (ms / 1e3) / 1e9,
+                              "us_per_32_row_block": ms * 1e3 / (2 * n / 32)}
+        SU = torch.empty_like(S0)
+        SU.copy_(S0)
+        binding.posit_rpotrf("U", n, SU, n, info, stream)
+        ms = _time_ms(lambda: binding.posit_rpotrs("U", n, 1, SU, n, b, n, stream), stream,
+                      setup=lambda: b.copy_(b0))
+        fac["rpotrs_U_8192"] = {"ms": ms, "us_per_32_row_block": ms * 1e3 / (2 * n / 32)}
+        del SU
         ms = _time_ms(lambda: binding.posit_rpotrs("L", n, 1, S, n, b, n, stream), stream, reps=1,
                       setup=lambda: b.copy_(b0))
         fac["rpotrs_8192"] = {"ms": ms, "note": "dot-form L^T solve: one serial chain of "
@@ -748,7 +760,7 @@ def extras(args, dev, stream):
 
     # batched: 4096 problems, n log-uniform [16, 512], half LU half Cholesky
     if want("batched"):
-        count = 4096
+        count = args.batch_count
         ns = inputs.batched_sizes(count, inputs.SEED_BASE + 3)
         info = torch.zeros(1, dtype=torch.int32, device=dev)
         batched = {}
@@ -764,7 +776,10 @@ def extras(args, dev, stream):
                 binding.posit_from_double(b64, ps.B[ps.b_off[i]:], k, stream)
             torch.cuda.synchronize()
             snap = ps.snapshot()
-            best, timings = autotune.tune_problem_set(ps, sample=None, use_cache=True)
+            if args.batch_plan:
+                best = tuple(int(v) for v in args.batch_plan.split(","))
+            else:
+                best, timings = autotune.tune_problem_set(ps, sample=None, use_cache=True)
             plan = plan_of(*best)
             ws = torch.empty(ps.workspace_bytes(plan), dtype=torch.uint8, device=dev)
             g = torch.cuda.CUDAGraph()

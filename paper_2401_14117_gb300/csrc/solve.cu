@@ -8,8 +8,8 @@
 //     descending k (column-oriented trsm; also the dot-form forward solve with
 //     ascending k).  x_i's last update needs x_{i-1} (in solve order), so the
 //     solve is one dependent step per unknown at best: a division, a product
-//     and a rounded subtraction.  trsv_pipe_kernel keeps that path in ONE warp
-//     and moves everything else off it (below).
+//     and a rounded subtraction.  trsv_pipe_kernel keeps that path in one
+//     warp and moves everything else off it (below).
 //   * "dot-form backward": x_i = (b_i - sum_{k = i+1 .. n-1, ascending}
 //     a_ki x_k) / a_ii, i descending (reference trsm Left-Lower-Transpose).
 //     x_i's first subtraction needs x_{i+1}, the last unknown to finish, so
@@ -41,19 +41,18 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // numbered J = 0, 1, ... in solve order (descending rows for a backward
 // solve).  Tile (I, J) holds the coefficients that block J's unknowns
 // contribute to block I's rows.  One right-hand side is one pipeline of warps:
-//   * the diagonal warp solves the blocks one after another.  While it solves
-//     block J (32 steps: divide x_t, broadcast it by a shuffle, apply it to
-//     the rows after t) it also brings block J+1 up to date: first with tile
-//     (J+1, J-1) from the unknowns of block J-1 (known), then with tile
-//     (J+1, J) as block J's unknowns become final -- two rounded
-//     multiply-subtracts per step on a chain that is independent of the
-//     diagonal one.  Its tiles are staged in shared memory by cp.async one
-//     block ahead.
+//   * the diagonal warp solves the blocks one after another (32 steps:
+//     divide x_t, broadcast it by a shuffle, apply it to the rows after t)
+//     and hands every unknown, as soon as it is final, to
+//   * the next-block warp (same CTA, through shared memory), which brings
+//     block J+1 up to date while block J is solved: tile (J+1, J-1) with the
+//     unknowns of block J-1 (all known), then tile (J+1, J) as block J's
+//     unknowns arrive; it hands block J+1 back to the diagonal warp and
+//     writes block J's unknowns to B;
 //   * helper warps bring every later block I up to date with tiles
-//     (I, 0) .. (I, I-3), each tile as soon as the diagonal warp has
-//     published that block's unknowns (a flag per block), and publish the
-//     partial sums of block I (another flag) one block-time before the
-//     diagonal warp needs them.
+//     (I, 0) .. (I, I-3), each tile as soon as its block's unknowns are
+//     published (a flag per block), and publish block I's partial sums
+//     (another flag) a block-time before the next-block warp needs them.
 // Every unknown still receives its updates in solve order, one rounded
 // multiply and one rounded subtract each, so the bits equal the sequential
 // loops'.  Solved values and the helpers' partial sums live in B itself.
@@ -225,6 +224,21 @@ __device__ __forceinline__ pz round_band(uint32_t sign, int S, uint32_t X) {
   return pz{S + (int)c, sign | (r >> c)};
 }
 
+// pz_to_bits of a rounded value that is not NaR, without branches: both
+// regime forms are built and selected (the clamps change nothing for the
+// regimes of rounded values, k in [-30, 30]; a zero's arbitrary scale is
+// overridden).
+__device__ __forceinline__ uint32_t bits_band(pz a) {
+  const int k = a.s >> 2;
+  const uint32_t body = ((uint32_t)(a.s & 3) << 27) | ((a.m & 0x3FFFFFFFu) >> 3);
+  const uint32_t kp = (uint32_t)min(max(k, 0), 30), kn = (uint32_t)min(max(-1 - k, 0), 29);
+  const uint32_t pos = (0x7FFFFFFFu ^ (0x7FFFFFFFu >> (kp + 1u))) | (body >> kp);
+  const uint32_t neg = (1u << (29u - kn)) | (body >> kn);
+  const uint32_t pay = k >= 0 ? pos : neg;
+  const uint32_t w = (a.m >> 31) ? (0u - pay) : pay;
+  return pz_is_zero(a) ? 0u : w;
+}
+
 // msub for in-band operands and a chain value as above.
 __device__ __forceinline__ pz msub_band(pz x, uint32_t aw, pz y) {
   uint32_t sg, X0, jam, Xs;
@@ -263,39 +277,59 @@ __device__ __forceinline__ pz div_recip(pz x, pz d, uint64_t R) {
   return round_band((x.m ^ d.m) & 0x80000000u, S, X);
 }
 
-// Shared memory of one CTA: the diagonal warp's tiles (D, C, S for three
-// blocks: the one being solved, the next, and the one after it, which is
-// staged while the current one is solved; used by the pipeline's first CTA
-// only) and two tiles per helper warp.
+// Shared memory of one CTA.  The pipeline's first CTA holds the diagonal
+// warp's tiles D = (J, J) and the next-block warp's tiles C = (J+1, J-1) and
+// S = (J+1, J), each for three blocks (in use, next, being staged); every
+// helper warp stages two tiles.
 constexpr int kTileWords = PB * PB;
-constexpr int kDiagBufs = 3;
-constexpr size_t kPipeSmem = (kDiagBufs * 3 + PWARPS * 2) * kTileWords * sizeof(uint32_t);
+constexpr int kBufs = 3;
+constexpr size_t kPipeSmem = (kBufs * 3 + PWARPS * 2) * kTileWords * sizeof(uint32_t);
 
-// Column t of the three tiles the diagonal warp uses for block J (D = (J, J),
-// C = (J+1, J-1), S = (J+1, J)), one cp.async per lane and tile.
-template <bool BW>
-__device__ __forceinline__ void stage_diag_column(const PipeArgs &a, uint32_t *buf, int J,
-                                                  int t) {
-  const int lane = threadIdx.x & 31;
-  const int nb = a.nblk;
-  const int I[3] = {J, J + 1, J + 1};
-  const int C[3] = {J, J - 1, J};
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    const bool blocks_ok = I[q] >= 0 && I[q] < nb && C[q] >= 0 && C[q] < nb;
-    const int64_t r = pipe_row0<BW>(blocks_ok ? I[q] : 0, nb) + lane;
-    const int64_t c = pipe_row0<BW>(blocks_ok ? C[q] : 0, nb) + t;
-    const bool ok = blocks_ok && r < a.n && c < a.n;
-    cp_async4(buf + q * kTileWords + t * PB + lane, ok ? pipe_elem(a, r, c) : a.A, ok);
+// The diagonal and next-block warps' exchange (static shared memory of the
+// first CTA).  slot[J & 1][s] = (J * 64 + s + 1) << 32 | word of block J's
+// unknown of step s: one 64-bit store carries the value and its tag, so the
+// reader needs no fence.
+struct PipeExchange {
+  unsigned long long slot[2][PB];
+  pz xh[PB];        // block J+1's sums through tile J, for the diagonal warp
+  int hand;         // J + 1 once xh holds them
+  int hand_clean;   // their chain is clean
+};
+
+// Bounded wait of a warp until `cond()` holds (shared-memory polls); false
+// after about 2 s (error flag set) or when another warp has given up.
+template <class Cond>
+__device__ bool warp_spin(Cond cond, int *err) {
+  unsigned long long t0 = 0;
+  for (unsigned polls = 1;; ++polls) {
+    if (__all_sync(0xFFFFFFFFu, cond())) return true;
+    if ((polls & 255u) == 0u) {
+      int stop = 0;
+      if ((threadIdx.x & 31) == 0) {
+        if (*(volatile int *)err) {
+          stop = 1;
+        } else {
+          const unsigned long long now = global_ns();
+          if (t0 == 0) {
+            t0 = now;
+          } else if (now - t0 > kWaitNs) {
+            atomicExch(err, 1);
+            stop = 1;
+          }
+        }
+      }
+      if (__shfl_sync(0xFFFFFFFFu, stop, 0)) return false;
+    }
   }
 }
 
-// (PT, 1): ptxas keeps enough registers for the three chains of a step to
+// (PT, 1): ptxas keeps enough registers for the chains of a step to
 // overlap; with its default budget they run one after another (measured
 // 953 against 651 cycles per step in a one-warp probe of the step).
 template <bool BW, bool UNIT>
 __global__ void __launch_bounds__(PT, 1) trsv_pipe_kernel(PipeArgs a) {
   extern __shared__ __align__(16) uint32_t psmem[];
+  __shared__ PipeExchange ex;
   const int lane = threadIdx.x & 31;
   const int wl = threadIdx.x >> 5;                 // warp within the CTA
   const int w = blockIdx.x * PWARPS + wl;          // warp within the pipeline
@@ -303,132 +337,196 @@ __global__ void __launch_bounds__(PT, 1) trsv_pipe_kernel(PipeArgs a) {
   uint32_t *b = a.B + (int64_t)blockIdx.y * a.ldb;
   int *solved = a.flags + (int64_t)blockIdx.y * 2 * nblk;
   int *ready = solved + nblk;  // 1: partial sums published from a clean chain, 2: not clean
-  if (a.abort_flag && *(volatile const int32_t *)a.abort_flag != 0) return;
   const unsigned FULL = 0xFFFFFFFFu;
+  if (a.abort_flag && *(volatile const int32_t *)a.abort_flag != 0) return;
+  if (blockIdx.x == 0) {
+    for (int i = threadIdx.x; i < 2 * PB; i += PT) (&ex.slot[0][0])[i] = 0ull;
+    if (threadIdx.x == 0) ex.hand = 0;
+  }
+  __syncthreads();
 
   if (w == 0) {
     // ------------------------------------------------ the diagonal warp
-    // Each step is straight-line code (every lane computes, selects keep
-    // the lanes that apply), so the diagonal chain (divide, broadcast,
-    // multiply-subtract), the chain of block J+1 and the staging of block
-    // J+2's tiles are interleaved by the compiler.  A block runs on the
-    // in-band forms when its tiles, the unknowns it uses and both chains
-    // qualify; a step whose new unknown leaves the band is redone on the
-    // general forms, as is the rest of that block.
-    uint32_t *tiles = psmem;  // [kDiagBufs][3][kTileWords]
-    for (int J0 = 0; J0 < 2; ++J0) {
-      for (int t = 0; t < PB; ++t) stage_diag_column<BW>(a, tiles + J0 * 3 * kTileWords, J0, t);
-      asm volatile("cp.async.commit_group;" ::: "memory");
-    }
+    // Solves the blocks one after another: per step, divide x_t, broadcast
+    // it, apply it to the rows after t -- straight-line code (every lane
+    // computes, selects keep the lanes that apply) -- and hand x_t to the
+    // next-block warp through shared memory.  A block runs on the in-band
+    // forms while its tile, its chain and the new unknowns qualify; a step
+    // whose unknown leaves the band is redone on the general forms, as is
+    // the rest of that block.
+    uint32_t *dt = psmem;  // [kBufs][kTileWords]: D of three blocks
+    stage_tile<BW>(a, dt, 0, 0);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    stage_tile<BW>(a, dt + kTileWords, 1, 1);
+    asm volatile("cp.async.commit_group;" ::: "memory");
     pz x = load_x(b, pipe_row0<BW>(0, nblk), a.n);
-    pz xn = nblk > 1 ? load_x(b, pipe_row0<BW>(1, nblk), a.n) : pz_zero();
-    pz xprev = pz_zero();
-    // the chains of x (block J) and xn (block J+1) are clean
-    bool cx = __all_sync(FULL, pz_band(x, 80)), cn = __all_sync(FULL, pz_band(xn, 80));
-    bool ok = true;
-    for (int J = 0; J < nblk && ok; ++J) {
-      asm volatile("cp.async.wait_group 1;" ::: "memory");  // block J's tiles are in
+    bool cx = __all_sync(FULL, pz_band(x, 80));
+    for (int J = 0; J < nblk; ++J) {
+      if (J > 0) {  // block J's sums through tile J-1, from the next-block warp
+        if (!warp_spin([&] { return *(volatile int *)&ex.hand >= J; }, a.err)) break;
+        x = ex.xh[lane];
+        cx = *(volatile int *)&ex.hand_clean != 0;
+      }
+      stage_tile<BW>(a, dt + ((J + 2) % kBufs) * kTileWords, J + 2, J + 2);
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
       __syncwarp();
-      const uint32_t *D = tiles + (J % kDiagBufs) * 3 * kTileWords;
-      const uint32_t *Cc = D + kTileWords, *Sx = D + 2 * kTileWords;
-      uint32_t *nxt = tiles + ((J + 2) % kDiagBufs) * 3 * kTileWords;
+      const uint32_t *D = dt + (J % kBufs) * kTileWords;
+      unsigned long long *slot = ex.slot[J & 1];
+      const unsigned long long tag = (unsigned long long)(J * 64) << 32;
       const int64_t row0 = pipe_row0<BW>(J, nblk);
       const int nr = (int)min64(PB, a.n - row0);
       if (lane >= nr) x = pz_zero();
       const pz dl = pz_decode(D[lane * PB + lane]);
       const uint64_t rl = UNIT ? 0ull : recip62(dl);
-      bool tok = pz_band(xprev, 40) && (UNIT || lane >= nr || (!pz_is_zero(dl)));
+      bool tok = UNIT || lane >= nr || !pz_is_zero(dl);
 #pragma unroll 8
-      for (int t = 0; t < PB; ++t)
-        tok &= word_band(D[t * PB + lane]) && word_band(Cc[t * PB + lane]) &&
-               word_band(Sx[t * PB + lane]);
-      tok = __all_sync(FULL, tok);
-      bool fast = cx && cn && tok;
-      bool xn_clean = cn && tok;  // every product xn receives in this block is in band
-      pz xnn = pz_zero();
-      bool cnn = false;
-      for (int half = 0; half < 2; ++half) {
-        if (half == 1 && J + 2 < nblk) {
-          // block J+2's partial sums, long published by its helper
-          if (!warp_wait(&ready[J + 2], a.err)) { ok = false; break; }
-          cnn = __ldcg(&ready[J + 2]) == 1;
-          xnn = load_x(b, pipe_row0<BW>(J + 2, nblk), a.n);
-        }
-        const uint32_t *T = half ? Sx : Cc;
-        const int s_end = (half + 1) * (PB / 2);
-        int s = half * (PB / 2);
-        // Each step: block J+1 gets two links on unknowns that are final
-        // before the step begins (so their shuffles do not wait for it):
-        // ua, ub (solve order) of block J-1 in the first half; of block J in
-        // the second half, one step behind (ua = -1 at its first step is a
-        // multiply by zero, and block J's last unknown follows the loop).
-        if (fast) {
+      for (int t = 0; t < PB; ++t) tok &= word_band(D[t * PB + lane]);
+      int s = 0;
+      if (cx && __all_sync(FULL, tok)) {
 #pragma unroll 1
-          for (; s < s_end; ++s) {
-            const int t = BW ? PB - 1 - s : s;
-            const int ua = half ? 2 * s - 33 : 2 * s, ub = ua + 1;
-            const int ta = BW ? PB - 1 - max(ua, 0) : max(ua, 0), tb = BW ? PB - 1 - ub : ub;
-            const pz src = half ? x : xprev;
-            pz ya = shfl_pz(src, ta);
-            const pz yb = shfl_pz(src, tb);
-            if (ua < 0) ya = pz_zero();
-            pz xs = x;
-            if (!UNIT) {
-              const pz q = div_recip(x, dl, rl);
-              const bool dv = lane == t && t < nr;
-              xs = pz{dv ? q.s : x.s, dv ? q.m : x.m};
-            }
-            const pz xt = shfl_pz(xs, t);
-            const pz r = msub_band(xs, D[t * PB + lane], xt);
-            const bool up = (BW ? lane < t : lane > t) && lane < nr;
-            xs = pz{up ? r.s : xs.s, up ? r.m : xs.m};
-            pz xns = msub_band(xn, T[ta * PB + lane], ya);
-            xns = msub_band(xns, T[tb * PB + lane], yb);
-            if (!pz_band(xt, 40)) break;  // the same on every lane: redo this step below
-            x = xs;
-            xn = xns;
-            stage_diag_column<BW>(a, nxt, J + 2, s);
-          }
-          if (s < s_end) fast = false;
-        }
-#pragma unroll 1
-        for (; s < s_end; ++s) {
+        for (; s < PB; ++s) {
           const int t = BW ? PB - 1 - s : s;
-          const int ua = half ? 2 * s - 33 : 2 * s, ub = ua + 1;
-          const int ta = BW ? PB - 1 - max(ua, 0) : max(ua, 0), tb = BW ? PB - 1 - ub : ub;
-          const pz src = half ? x : xprev;
-          pz ya = shfl_pz(src, ta);
-          const pz yb = shfl_pz(src, tb);
-          if (ua < 0) ya = pz_zero();
+          pz xs = x;
           if (!UNIT) {
-            const pz q = pz_div_inline(x, dl);
+            const pz q = div_recip(x, dl, rl);
             const bool dv = lane == t && t < nr;
-            x = pz{dv ? q.s : x.s, dv ? q.m : x.m};
+            xs = pz{dv ? q.s : x.s, dv ? q.m : x.m};
           }
-          const pz xt = shfl_pz(x, t);
-          xn_clean = xn_clean && pz_band(xt, 40);
-          const pz r = msub(x, D[t * PB + lane], xt);
+          const pz xt = shfl_pz(xs, t);
+          const pz r = msub_band(xs, D[t * PB + lane], xt);
           const bool up = (BW ? lane < t : lane > t) && lane < nr;
-          x = pz{up ? r.s : x.s, up ? r.m : x.m};
-          xn = msub(xn, T[ta * PB + lane], ya);
-          xn = msub(xn, T[tb * PB + lane], yb);
-          stage_diag_column<BW>(a, nxt, J + 2, s);
-        }
-        if (half == 1) {  // block J's last unknown into block J+1
-          const int tl = BW ? 0 : PB - 1;
-          const pz yl = shfl_pz(x, tl);
-          xn = fast ? msub_band(xn, Sx[tl * PB + lane], yl) : msub(xn, Sx[tl * PB + lane], yl);
+          xs = pz{up ? r.s : xs.s, up ? r.m : xs.m};
+          if (!pz_band(xt, 40)) break;  // the same on every lane: redo this step below
+          x = xs;
+          if (lane == 0)
+            *(volatile unsigned long long *)&slot[s] =
+                tag + ((unsigned long long)(s + 1) << 32) + bits_band(xt);
         }
       }
+#pragma unroll 1
+      for (; s < PB; ++s) {
+        const int t = BW ? PB - 1 - s : s;
+        if (!UNIT) {
+          const pz q = pz_div_inline(x, dl);
+          const bool dv = lane == t && t < nr;
+          x = pz{dv ? q.s : x.s, dv ? q.m : x.m};
+        }
+        const pz xt = shfl_pz(x, t);
+        const pz r = msub(x, D[t * PB + lane], xt);
+        const bool up = (BW ? lane < t : lane > t) && lane < nr;
+        x = pz{up ? r.s : x.s, up ? r.m : x.m};
+        if (lane == 0)
+          *(volatile unsigned long long *)&slot[s] =
+              tag + ((unsigned long long)(s + 1) << 32) + pz_to_bits(xt);
+      }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    return;
+  }
+
+  if (w == 1) {
+    // ------------------------------------------------ the next-block warp
+    // While the diagonal warp solves block J, brings block J+1 up to date:
+    // its partial sums through tile J-2 come from a helper; tile (J+1, J-1)
+    // uses block J-1's unknowns (known: the products first, then the chain
+    // of additions); tile (J+1, J) takes block J's unknowns from the
+    // exchange slots as they become final.  Then hands block J+1 to the
+    // diagonal warp and writes block J's unknowns to B (flag `solved`).
+    uint32_t *nt = psmem + kBufs * kTileWords;  // [kBufs][C, S][kTileWords]
+    stage_tile<BW>(a, nt, 1, -1);
+    stage_tile<BW>(a, nt + kTileWords, 1, 0);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    stage_tile<BW>(a, nt + 2 * kTileWords, 2, 0);
+    stage_tile<BW>(a, nt + 3 * kTileWords, 2, 1);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    pz xprev = pz_zero();  // block J-1's unknowns (lane t: the one of row t)
+    for (int J = 0; J < nblk; ++J) {
+      const bool has_next = J + 1 < nblk;
+      pz xn = pz_zero();
+      bool clean = false;
+      if (has_next) {
+        if (J + 1 >= 2) {
+          if (!warp_wait(&ready[J + 1], a.err)) break;
+          clean = __ldcg(&ready[J + 1]) == 1;
+          xn = load_x(b, pipe_row0<BW>(J + 1, nblk), a.n);
+        } else {
+          xn = load_x(b, pipe_row0<BW>(J + 1, nblk), a.n);
+          clean = __all_sync(FULL, pz_band(xn, 80));
+        }
+      }
+      uint32_t *nb = nt + ((J + 2) % kBufs) * 2 * kTileWords;
+      stage_tile<BW>(a, nb, J + 3, J + 1);
+      stage_tile<BW>(a, nb + kTileWords, J + 3, J + 2);
       asm volatile("cp.async.commit_group;" ::: "memory");
-      if (!ok) break;
-      store_x(b, row0, a.n, x);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+      __syncwarp();
+      const uint32_t *Cc = nt + (J % kBufs) * 2 * kTileWords, *Sx = Cc + kTileWords;
+      bool tok = pz_band(xprev, 40);
+#pragma unroll 8
+      for (int t = 0; t < PB; ++t) tok &= word_band(Cc[t * PB + lane]) && word_band(Sx[t * PB + lane]);
+      clean = clean && __all_sync(FULL, tok);
+      if (has_next) {
+        // tile (J+1, J-1): every product first, then the chain
+        if (clean) {
+          pz p[PB];
+#pragma unroll
+          for (int u = 0; u < PB; ++u) {
+            const int t = BW ? PB - 1 - u : u;
+            uint32_t sg, X0, jam;
+            int S;
+            pz_mul_parts(decode_band(Cc[t * PB + lane]), shfl_pz(xprev, t), sg, S, X0, jam);
+            p[u] = round_band(sg, S, X0 | jam);
+          }
+#pragma unroll
+          for (int u = 0; u < PB; ++u) {
+            uint32_t sg, X;
+            int S;
+            pz_add_exact_inband(xn, pz{p[u].s, p[u].m ^ 0x80000000u}, sg, S, X);
+            xn = round_band(sg, S, X);
+          }
+        } else {
+#pragma unroll 1
+          for (int u = 0; u < PB; ++u) {
+            const int t = BW ? PB - 1 - u : u;
+            xn = msub(xn, Cc[t * PB + lane], shfl_pz(xprev, t));
+          }
+        }
+      }
+      // tile (J+1, J) as block J's unknowns become final
+      const unsigned long long *slot = ex.slot[J & 1];
+      pz xcur = pz_zero();
+      bool gave_up = false;
+#pragma unroll 1
+      for (int u = 0; u < PB; ++u) {
+        const unsigned long long want = ((unsigned long long)(J * 64 + u + 1)) << 32;
+        if (!warp_spin([&] {
+              return (*(volatile const unsigned long long *)&slot[u] & 0xFFFFFFFF00000000ull) ==
+                     want;
+            }, a.err)) {
+          gave_up = true;
+          break;
+        }
+        const pz y = pz_decode((uint32_t)*(volatile const unsigned long long *)&slot[u]);
+        const int t = BW ? PB - 1 - u : u;
+        if (lane == t) xcur = y;
+        if (has_next) {
+          const bool ok = clean && pz_band(y, 40);
+          clean = ok;
+          xn = ok ? msub_band(xn, Sx[t * PB + lane], y) : msub(xn, Sx[t * PB + lane], y);
+        }
+      }
+      if (gave_up) break;
+      if (has_next) {
+        ex.xh[lane] = xn;
+        if (lane == 0) ex.hand_clean = clean;
+        __threadfence_block();
+        __syncwarp();
+        if (lane == 0) *(volatile int *)&ex.hand = J + 1;
+      }
+      store_x(b, pipe_row0<BW>(J, nblk), a.n, xcur);
       warp_publish(&solved[J]);
-      xprev = x;
-      x = xn;
-      cx = xn_clean;
-      xn = xnn;
-      cn = cnn;
+      xprev = xcur;
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     return;
@@ -441,9 +539,9 @@ __global__ void __launch_bounds__(PT, 1) trsv_pipe_kernel(PipeArgs a) {
   // and unknowns are all in band, applied to clean chains, runs on the
   // in-band forms.  Bit k of `dirty` marks the helper's k-th block as not
   // clean (blocks past the 32nd are treated as not clean).
-  uint32_t *ht = psmem + (kDiagBufs * 3 + wl * 2) * kTileWords;  // [2][kTileWords]
-  const int H = gridDim.x * PWARPS - 1;
-  const int h = w - 1;
+  uint32_t *ht = psmem + (kBufs * 3 + wl * 2) * kTileWords;  // [2][kTileWords]
+  const int H = gridDim.x * PWARPS - 2;
+  const int h = w - 2;
   int Ilast = -1;
   for (int I = 2 + h; I < nblk; I += H) Ilast = I;
   if (Ilast < 0) return;
@@ -702,8 +800,8 @@ int trsv_pipe(const uint32_t *A, int64_t lda, int trans, int backward, int unit,
   const int64_t resident = (int64_t)per_sm * l.sms;
   // one block per helper warp keeps the helpers ahead of the diagonal warp;
   // with fewer co-resident warps each helper takes several blocks (slower)
-  const int64_t helpers = max64(3, nblk - 2);
-  const int64_t gx = min64(ceil_div(helpers + 1, PWARPS), resident);
+  const int64_t helpers = max64(2, nblk - 2);
+  const int64_t gx = min64(ceil_div(helpers + 2, PWARPS), resident);
   int64_t chunk = min64(NRHS_CHUNK, (int64_t)((scratch_bytes - kPipeHead) / per_rhs));
   chunk = max64(1, min64(chunk, resident / gx));
   for (int64_t c0 = 0; c0 < nrhs; c0 += chunk) {
