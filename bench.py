@@ -98,7 +98,7 @@ def parse():
                    help="threads,ctas_per_sm,smem_bytes for the batched section (default: autotuned)")
     p.add_argument("--serve-pool", type=int, default=96,
                    help="seeded problems in the serving pool")
-    p.add_argument("--serve-rates", default="40,80,120,160,240,320,480",
+    p.add_argument("--serve-rates", default="40,80,120,160,200,240,320,480",
                    help="arrival rates of the serving_sweep section")
     p.add_argument("--serve-slo-ms", type=float, default=250.0,
                    help="p99 latency objective of the serving_sweep section")
@@ -861,7 +861,9 @@ def extras(args, dev, stream):
                 r.pop("kept")
                 r["rate"] = rate
                 rows.append(r)
-                if r["p99_ms"] is not None and r["p99_ms"] <= slo and r["censored"] == 0:
+                # p99 over every offered request, the unfinished ones at their
+                # wait so far: a run that falls behind shows it there
+                if r["p99_ms"] is not None and r["p99_ms"] <= slo:
                     best = rate
             sweep[name] = {"runs": rows, "highest_rate_within_slo": best}
         del pool

@@ -798,11 +798,17 @@ int trsv_pipe(const uint32_t *A, int64_t lda, int trans, int backward, int unit,
       per_sm < 1)
     return POSIT_ERR_CUDA;
   const int64_t resident = (int64_t)per_sm * l.sms;
-  // one block per helper warp keeps the helpers ahead of the diagonal warp;
-  // with fewer co-resident warps each helper takes several blocks (slower)
-  const int64_t helpers = max64(2, nblk - 2);
-  const int64_t gx = min64(ceil_div(helpers + 2, PWARPS), resident);
-  int64_t chunk = min64(NRHS_CHUNK, (int64_t)((scratch_bytes - kPipeHead) / per_rhs));
+  // One block per helper warp keeps the helpers well ahead of the pipeline;
+  // down to about two blocks per helper they still keep up (two chains per
+  // lane), so fewer helpers are used when that lets every right-hand side of
+  // the chunk run in one launch.  With fewer co-resident warps than that
+  // each helper takes more blocks (slower, still correct).
+  int64_t chunk = min64(min64(NRHS_CHUNK, nrhs),
+                        (int64_t)((scratch_bytes - kPipeHead) / per_rhs));
+  chunk = max64(1, chunk);
+  const int64_t gx_full = ceil_div(max64(2, nblk - 2) + 2, PWARPS);
+  const int64_t gx_min = ceil_div(max64(2, (nblk - 1) / 2) + 2, PWARPS);
+  const int64_t gx = min64(max64(gx_min, min64(gx_full, resident / chunk)), resident);
   chunk = max64(1, min64(chunk, resident / gx));
   for (int64_t c0 = 0; c0 < nrhs; c0 += chunk) {
     const int64_t nc = min64(chunk, nrhs - c0);

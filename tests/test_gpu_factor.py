@@ -366,26 +366,30 @@ def test_solve_workload_2048():
     assert_same(from_dev(dB), want, "potrs workload")
 
 
-@pytest.mark.parametrize("kind", ["getrs", "potrs"])
-def test_solve_8192_synthetic_factors(kind):
-    """n = 8192, 1 RHS: the solve alone on seeded factor-shaped matrices
-    (the oracle cannot factor n = 8192 in test time): unit-lower L and upper U
-    (or L with positive diagonal) with uniform entries and a random valid
-    pivot vector."""
+@pytest.mark.parametrize("kind,nrhs", [("getrs", 1), ("potrs", 1), ("getrs", 8), ("potrs_U", 8)])
+def test_solve_8192_synthetic_factors(kind, nrhs):
+    """n = 8192: the solve alone on seeded factor-shaped matrices (the oracle
+    cannot factor n = 8192 in test time): unit-lower L and upper U (or L / U
+    with positive diagonal) with uniform entries and a random valid pivot
+    vector.  With 8 right-hand sides the eight pipelines share one launch,
+    so some helper warps bring two blocks up to date."""
     n = 8192
     rng = np.random.default_rng(8192)
     F = words((n, n), inputs.SEED_BASE + 8)
     d = np.arange(n)
     F[d, d] = oracle.from_double_array(rng.uniform(1.0, 2.0, n))
-    b = words((n, 1), inputs.SEED_BASE + 9)
+    b = words((n, nrhs), inputs.SEED_BASE + 9)
     dF, dB = to_dev(F), to_dev(b)
     if kind == "getrs":
         ipiv = (d + rng.integers(0, 16, n)).clip(max=n - 1).astype(np.int32) + 1
         want = oracle.rgetrs(F, ipiv, b)
-        binding.posit_rgetrs("N", n, 1, dF, n, torch.from_numpy(ipiv).to(DEV), dB, n)
+        binding.posit_rgetrs("N", n, nrhs, dF, n, torch.from_numpy(ipiv).to(DEV), dB, n)
+    elif kind == "potrs_U":
+        want = oracle.rpotrs(F, b, uplo="U")
+        binding.posit_rpotrs("U", n, nrhs, dF, n, dB, n)
     else:
         want = oracle.rpotrs(F, b)
-        binding.posit_rpotrs("L", n, 1, dF, n, dB, n)
+        binding.posit_rpotrs("L", n, nrhs, dF, n, dB, n)
     torch.cuda.synchronize()
     assert_same(from_dev(dB), want, kind)
 
