@@ -443,12 +443,16 @@ constexpr int TRSM_T = 256;
 constexpr int TRSM_CHUNK = 16;
 constexpr int TRSM_MAXJB = 256;
 
-__device__ __forceinline__ bool trsm_out_of_band(pz v) {
-  return !pz_is_zero(v) && (v.s < -40 || v.s > 40);
+// A value that is not zero and has its scale outside [-lim, lim] (NaR too).
+__device__ __forceinline__ bool trsm_outside(pz v, int lim) {
+  return !pz_is_zero(v) && (v.s < -lim || v.s > lim);
 }
 
 __global__ void __launch_bounds__(TRSM_T)
-trsm_llu_kernel(uint32_t *__restrict__ A, int64_t lda, int64_t j, int jb, int64_t c0, int64_t c1) {
+trsm_llu_kernel(uint32_t *__restrict__ A, int64_t lda, int64_t j, int jb, int64_t c0, int64_t c1,
+                uint32_t neg1) {
+  // neg1 = 0xFFFFFFFF: the multiplier of the in-band addition's operand pick
+  // (pz_add_inband_blend), an argument so that it stays a multiply-add
   __shared__ pz Ls[TRSM_CHUNK][TRSM_MAXJB];  // Ls[u][r] = l_{r, t0+u}
   __shared__ pz_rtab tab_in[256];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -457,19 +461,21 @@ trsm_llu_kernel(uint32_t *__restrict__ A, int64_t lda, int64_t j, int jb, int64_
   for (int i = tid; i < 256; i += TRSM_T) tab_in[i] = pz_rtab_inband_entry(i);
   uint32_t *cp = A + j + col * lda;
   pz xs[TRSM_MAXJB / 32];
-  bool oob = false;
+  bool far = false;
 #pragma unroll
   for (int i = 0; i < TRSM_MAXJB / 32; ++i) {
     const int r = 32 * i + lane;
     xs[i] = (active && r < jb) ? pz_decode(cp[r]) : pz_zero();
-    oob |= trsm_out_of_band(xs[i]);
+    far |= trsm_outside(xs[i], 80);
   }
-  // In-band steps: while l_{r,t}, u_t and the row's value are zero or have
-  // scales in [-40, 40], one rounded x - l u stays within the scales
-  // [-107, 82] and needs no test for the regimes of 28 or more bits (NaR is
-  // out of band).  The column's values are checked after every step, the
-  // chunk of L11 when it is loaded.
-  bool x_ok = !__any_sync(0xFFFFFFFFu, oob);
+  // In-band steps (the bound argument of the Rgemm kernel): while every
+  // product has operands l_{r,t}, u_t that are zero or of scale in [-40, 40]
+  // and the column's values started at scales within [-80, 80], every value
+  // of the column stays a multiple of 2^-107 below 2^89, so no rounding needs
+  // the test for the regimes of 28 or more bits.  So the checks are: the
+  // column once (and again after any general step), the chunk of L11 when it
+  // is loaded, and u_t -- a column value used as a multiplier -- at its step.
+  bool chain_ok = !__any_sync(0xFFFFFFFFu, far);
 #pragma unroll
   for (int i0 = 0; i0 < TRSM_MAXJB / 32; ++i0) {
     if (32 * i0 >= jb - 1) break;  // rows from 32*i0 on have nothing below them to update
@@ -483,7 +489,7 @@ trsm_llu_kernel(uint32_t *__restrict__ A, int64_t lda, int64_t j, int jb, int64_
         const int u = idx / jb, r = idx - u * jb;
         const int t = t0 + u;
         const pz v = (r > t && t < jb) ? pz_decode(A[(j + r) + (j + t) * lda]) : pz_zero();
-        l_bad |= trsm_out_of_band(v);
+        l_bad |= trsm_outside(v, 40);
         Ls[u][r] = v;
       }
       const bool l_ok = !__syncthreads_or(l_bad);
@@ -494,29 +500,24 @@ trsm_llu_kernel(uint32_t *__restrict__ A, int64_t lda, int64_t j, int jb, int64_
           const int owner = t & 31;
           const pz xt{__shfl_sync(0xFFFFFFFFu, xs[i0].s, owner),
                       __shfl_sync(0xFFFFFFFFu, xs[i0].m, owner)};
-          if (l_ok && x_ok) {  // warp-uniform
-            oob = false;
+          if (l_ok && chain_ok && !trsm_outside(xt, 40)) {  // warp-uniform
 #pragma unroll
             for (int i = i0; i < TRSM_MAXJB / 32; ++i) {
               const int r = 32 * i + lane;
               if (r > t && r < jb) {
                 const pz p = pz_mul_inband(tab_in, Ls[u][r], xt);
-                xs[i] = pz_add_inband(tab_in, xs[i], pz{p.s, p.m ^ 0x80000000u});
-                oob |= trsm_out_of_band(xs[i]);
+                xs[i] = pz_add_inband_blend(tab_in, neg1, xs[i], pz{p.s, p.m ^ 0x80000000u});
               }
             }
-            x_ok = !__any_sync(0xFFFFFFFFu, oob);
           } else {
-            oob = false;
+            far = false;
 #pragma unroll
             for (int i = i0; i < TRSM_MAXJB / 32; ++i) {
               const int r = 32 * i + lane;
-              if (r > t && r < jb) {
-                xs[i] = pz_sub(xs[i], pz_mul(Ls[u][r], xt));
-                oob |= trsm_out_of_band(xs[i]);
-              }
+              if (r > t && r < jb) xs[i] = pz_sub(xs[i], pz_mul(Ls[u][r], xt));
+              far |= trsm_outside(xs[i], 80);
             }
-            x_ok = !__any_sync(0xFFFFFFFFu, oob);
+            chain_ok = !__any_sync(0xFFFFFFFFu, far);  // a new start for the argument
           }
         }
       }
@@ -633,7 +634,7 @@ int trsm_llu(uint32_t *A, int64_t lda, int64_t j, int jb, int64_t c0, int64_t c1
   if (c1 <= c0 || jb <= 1) return POSIT_OK;
   if (jb > TRSM_MAXJB) return POSIT_ERR_DEVICE;  // never: panels are at most kNB wide
   dim3 grid((unsigned)ceil_div(c1 - c0, TRSM_T / 32));
-  trsm_llu_kernel<<<grid, TRSM_T, 0, stream>>>(A, lda, j, jb, c0, c1);
+  trsm_llu_kernel<<<grid, TRSM_T, 0, stream>>>(A, lda, j, jb, c0, c1, 0xFFFFFFFFu);
   return launch_status();
 }
 
