@@ -15,11 +15,14 @@
 //     x_i's first subtraction needs x_{i+1}, the last unknown to finish, so
 //     the n(n-1)/2 subtractions form one serial chain per right-hand side.
 //     trsv_dot_backward_kernel computes the products of each row in parallel
-//     and runs the chain of rounded subtractions in one thread.
+//     and runs the chain of rounded additions in one thread, in the signed
+//     chain form of chain.cuh (about half the instructions of a general
+//     addition per link).
 //
 // Row swaps (ipiv, LAPACK convention) are applied by a one-CTA-per-column
 // kernel on a shared-memory copy of the column.
 #include "internal.cuh"
+#include "chain.cuh"
 
 namespace posit {
 namespace {
@@ -630,58 +633,78 @@ __global__ void __launch_bounds__(PT, 1) trsv_pipe_kernel(PipeArgs a) {
 // x_i = (b_i - sum_{k>i, ascending} a(k, i) x_k) / a(i, i), i = n-1 .. 0,
 // for one right-hand side per CTA (column blockIdx.x of B).  a(k, i) is
 // A[k + i*lda] (column i below the diagonal).  The products of a row are
-// formed in parallel (the next chunk while the current one is consumed) and
-// stored negated; one thread runs the chain of rounded additions, the only
-// serial part, with the short-path addition pz_add_serial (a NaR product or
-// b_i makes x_i NaR; that test is off the chain's dependency path).
-__global__ void __launch_bounds__(ST) trsv_dot_backward_kernel(const uint32_t *__restrict__ A,
+// formed in parallel (the next 256 while the current 256 are consumed),
+// stored negated in the signed chain form with a bit per product that is NaR
+// or outside the chain band; one thread runs the chain of rounded additions,
+// the only serial part, in runs of PZS_RUN links by pzs_link, and takes
+// pzs_link_general for a run whose start value or products are outside the
+// band or whose sums cancelled two or more bits (a NaR product or b_i makes
+// x_i NaR on that path).
+constexpr size_t kDotStatic = 2 * ST * sizeof(pzs) + 2 * (ST / 32) * sizeof(unsigned) +
+                              256 * sizeof(pzs_rtab);
+
+__global__ void __launch_bounds__(ST, 1) trsv_dot_backward_kernel(const uint32_t *__restrict__ A,
                                                                 int64_t lda, uint32_t *B,
                                                                 int64_t ldb, int64_t n, int unit,
                                                                 const int32_t *abort_flag) {
-  __shared__ pz prod[2][ST + 1];
+  static_assert(ST == 256 && PZS_RUN == 32, "one table entry per thread; a run per bad-bit word");
+  __shared__ pzs prod[2][ST];
+  __shared__ unsigned bad[2][ST / 32];  // bit q of word w: product 32 w + q is NaR or out of band
+  __shared__ pzs_rtab tab[256];
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pz *x = reinterpret_cast<pz *>(smem_raw);  // [n] the right-hand side / solution
   uint32_t *b = B + (int64_t)blockIdx.x * ldb;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (abort_flag && *abort_flag != 0) return;
+  tab[tid] = pzs_rtab_entry(tid);
   for (int64_t i = tid; i < n; i += ST) x[i] = pz_decode(b[i]);
   __syncthreads();
   for (int64_t i = n - 1; i >= 0; --i) {
     const uint32_t *col = A + i * lda;
-    {
-      int64_t k = i + 1 + tid;
+    // the negated products -a(k, i) x_k for k in [k0, k0 + ST) (zero past n)
+    auto produce = [&](int64_t k0, int buf) {
+      const int64_t k = k0 + tid;
+      pzs p{PZS_ZERO_S, 0};
       if (k < n) {
-        pz p = pz_mul(pz_decode(col[k]), x[k]);
-        prod[0][tid] = pz{p.s, p.m ^ 0x80000000u};
+        const pz q = pz_mul(pz_decode(col[k]), x[k]);
+        p = pzs_of(pz{q.s, q.m ^ 0x80000000u});
       }
-    }
+      prod[buf][tid] = p;
+      const unsigned m = __ballot_sync(0xFFFFFFFFu, !pzs_in_band(p));
+      if (lane == 0) bad[buf][warp] = m;
+    };
+    if (i + 1 < n) produce(i + 1, 0);
     __syncthreads();
-    pz acc = x[i];
-    bool nar = pz_is_nar(acc);
+    pzs acc = pzs_of(x[i]);
     int buf = 0;
     for (int64_t k0 = i + 1; k0 < n; k0 += ST) {
-      int64_t kn = k0 + ST + tid;
-      if (kn < n) {
-        pz p = pz_mul(pz_decode(col[kn]), x[kn]);
-        prod[buf ^ 1][tid] = pz{p.s, p.m ^ 0x80000000u};
-      }
+      if (k0 + ST < n) produce(k0 + ST, buf ^ 1);
       if (tid == 0) {
-        const int cnt = (int)min64(ST, n - k0);
-        const pz *pr = prod[buf];
-        pz pn = pr[0];
-#pragma unroll 4
-        for (int t = 0; t < cnt; ++t) {
-          const pz p = pn;
-          pn = pr[t + 1];  // next link's product, loaded ahead (row padded by one)
-          nar |= p.s >= PZ_NAR_T;
-          acc = pz_add_serial(acc, p);
+        const pzs *pr = prod[buf];
+        const unsigned *bw = bad[buf];
+        const int runs = (int)((min64(ST, n - k0) + PZS_RUN - 1) / PZS_RUN);
+        for (int r = 0; r < runs; ++r) {
+          const pzs save = acc;
+          const pzs *pt = pr + PZS_RUN * r;
+          const unsigned bits = bw[r];
+          bool general = (bits != 0u) | !pzs_in_band(save);
+          if (!general) {
+            uint32_t fmin = 0xFFFFFFFFu;
+#pragma unroll
+            for (int u = 0; u < PZS_RUN; ++u) pzs_link(acc, pt[u], tab, fmin);
+            general = fmin < 0x20000000u;
+          }
+          if (general) {
+            acc = save;
+            for (int u = 0; u < PZS_RUN; ++u) acc = pzs_link_general(acc, pt[u]);
+          }
         }
       }
       __syncthreads();
       buf ^= 1;
     }
     if (tid == 0) {
-      pz v = nar ? pz_nar() : pz_canon(acc, false);
+      pz v = pz_of(acc);
       if (!unit) v = pz_div(v, pz_decode(col[i]));
       x[i] = v;
     }
@@ -832,7 +855,7 @@ int trsv_dot_backward(const uint32_t *A, int64_t lda, int unit, uint32_t *B, int
                       int64_t n, int64_t nrhs, const Limits &l, cudaStream_t stream,
                       const int32_t *abort_flag = nullptr) {
   size_t smem = (size_t)n * sizeof(pz);
-  if (smem + 4096 <= (size_t)l.smem_optin) {
+  if (smem + kDotStatic + 1024 <= (size_t)l.smem_optin) {
     if (cudaFuncSetAttribute(trsv_dot_backward_kernel,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return POSIT_ERR_CUDA;

@@ -292,8 +292,14 @@ def _chain_factor(case, n, rng):
     scale (long regimes, saturation), 'cancel' -- entries +-2^j with small
     right-hand sides, so that sums cancel one or many bits or vanish, 'edges'
     -- magnitudes near 2^+-106, where the result scale meets the long-regime
-    band.  Zeros are sprinkled in; U (for Rgetrs) is the identity."""
-    if case == "range":
+    band, 'high' / 'low' -- entries of size 1 with right-hand sides near 2^55 /
+    2^-74, so that the running sums cross the scales 56 and -75 where runs of
+    links leave the signed fast form.  Zeros are sprinkled in; U (for Rgetrs) is
+    the identity."""
+    if case in ("high", "low"):
+        v = rng.uniform(0.25, 2.0, size=(n, n)) * rng.choice([-1.0, 1.0], size=(n, n))
+        F = oracle.from_double_array(v)
+    elif case == "range":
         F = mixed_words(rng, n * n).reshape(n, n)
         F[F == 0x80000000] = ONE
     elif case == "cancel":
@@ -310,7 +316,7 @@ def _chain_factor(case, n, rng):
     return F
 
 
-@pytest.mark.parametrize("case", ["range", "cancel", "edges"])
+@pytest.mark.parametrize("case", ["range", "cancel", "edges", "high", "low"])
 @pytest.mark.parametrize("kind", ["getrs_T", "potrs_L"])
 def test_dot_form_chain_paths(case, kind):
     n, nrhs = 300, 3
@@ -321,6 +327,9 @@ def test_dot_form_chain_paths(case, kind):
         B[B == 0x80000000] = 0
     elif case == "cancel":
         B = oracle.from_double_array(rng.uniform(-0.01, 0.01, size=(n, nrhs)))
+    elif case in ("high", "low"):
+        B = oracle.from_double_array(
+            np.ldexp(rng.uniform(-2, 2, size=(n, nrhs)), 55 if case == "high" else -74))
     else:
         B = oracle.from_double_array(np.ldexp(rng.uniform(-2, 2, size=(n, nrhs)), 106))
     B[rng.random((n, nrhs)) < 0.05] = 0
