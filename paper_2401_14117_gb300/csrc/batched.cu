@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "chain.cuh"
 
 namespace posit {
 namespace {
@@ -398,7 +399,7 @@ __device__ void getrs_decoded(const pz *M, int n, const int32_t *ipiv, pz *X, in
 }
 
 // Rpotrs 'L' on the decoded factor: L y = b then the dot-form L^T x = y.
-__device__ void potrs_decoded(const pz *M, int n, pz *X, int nrhs, pz *prod) {
+__device__ void potrs_decoded(const pz *M, int n, pz *X, int nrhs, pz *prod, const pzs_rtab *tab) {
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int j = 0; j < n; ++j) {
     for (int c = tid; c < nrhs; c += nt) X[j + c * n] = pz_div(X[j + c * n], M[j + (size_t)j * n]);
@@ -410,31 +411,30 @@ __device__ void potrs_decoded(const pz *M, int n, pz *X, int nrhs, pz *prod) {
     }
     __syncthreads();
   }
-  // x_i = (y_i - sum_{k>i, ascending} l_ki x_k) / l_ii: products in parallel
-  // (stored negated), one serial chain of short-path additions per right-hand side;
-  // a NaR product or y_i makes x_i NaR
+  // x_i = (y_i - sum_{k>i, ascending} l_ki x_k) / l_ii: products in parallel,
+  // stored negated in the signed chain form (chain.cuh), one serial chain per
+  // right-hand side in checked runs of PZS_RUN links; a row with a product
+  // that is NaR or outside the chain band runs on the general addition (a
+  // NaR product or y_i makes x_i NaR there)
+  pzs *pr_all = reinterpret_cast<pzs *>(prod);
   for (int i = n - 1; i >= 0; --i) {
     const int m = n - i - 1;
+    int bad = 0;
     for (int idx = tid; idx < m * nrhs; idx += nt) {
       int k = i + 1 + idx % m, c = idx / m;
-      pz p = pz_mul(M[k + (size_t)i * n], X[k + c * n]);
-      prod[idx] = pz{p.s, p.m ^ 0x80000000u};
+      const pz p = pz_mul(M[k + (size_t)i * n], X[k + c * n]);
+      const pzs q = pzs_of(pz{p.s, p.m ^ 0x80000000u});
+      bad |= !pzs_in_band(q);
+      pr_all[idx] = q;
     }
-    __syncthreads();
+    const bool products_ok = !__syncthreads_or(bad);
     for (int c = tid; c < nrhs; c += nt) {
-      pz acc = X[i + c * n];
-      bool nar = pz_is_nar(acc);
-      const pz *pr = prod + c * m;
-      pz pn = pr[0];
-#pragma unroll 4
-      for (int t = 0; t < m; ++t) {
-        const pz p = pn;
-        pn = pr[t + 1];  // loaded ahead; prod holds n * max(nrhs, 1) > m * nrhs entries
-        nar |= p.s >= PZ_NAR_T;
-        acc = pz_add_serial(acc, p);
-      }
-      acc = nar ? pz_nar() : pz_canon(acc, false);
-      X[i + c * n] = pz_div(acc, M[i + (size_t)i * n]);
+      pzs acc = pzs_of(X[i + c * n]);
+      const pzs *pr = pr_all + c * m;
+      int t = 0;
+      for (; t + PZS_RUN <= m; t += PZS_RUN) pzs_run<PZS_RUN>(acc, pr + t, PZS_RUN, tab, products_ok);
+      if (t < m) pzs_run<0>(acc, pr + t, m - t, tab, products_ok);
+      X[i + c * n] = pz_div(pz_of(acc), M[i + (size_t)i * n]);
     }
     __syncthreads();
   }
@@ -452,10 +452,12 @@ __global__ void __launch_bounds__(512) batched_kernel(const posit_problem *__res
   __shared__ int s_nar;
   __shared__ pz_rtab rtab[256];
   __shared__ pz_rtab rtab_in[256];
+  __shared__ pzs_rtab ctab[256];  // the serial chain's rounding constants
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int i = tid; i < 256; i += nt) {
     rtab[i] = pz_rtab_entry(i);
     rtab_in[i] = pz_rtab_inband_entry(i);
+    ctab[i] = pzs_rtab_entry(i);
   }
   pz *ws = workspace + (size_t)blockIdx.x * ws_elems_per_cta;
   for (;;) {
@@ -508,7 +510,7 @@ __global__ void __launch_bounds__(512) batched_kernel(const posit_problem *__res
     } else if (P.kind == POSIT_CHOLESKY) {
       info = fast ? chol_decoded<true>(M, n, sh, rtab, rtab_in, ib0)
                   : chol_decoded<false>(M, n, sh, rtab, rtab_in, false);
-      if (info == 0) potrs_decoded(M, n, X, nrhs, prod);
+      if (info == 0) potrs_decoded(M, n, X, nrhs, prod, ctab);
     } else {
       info = fast ? chol_decoded<true>(M, n, sh, rtab, rtab_in, ib0)
                   : chol_decoded<false>(M, n, sh, rtab, rtab_in, false);

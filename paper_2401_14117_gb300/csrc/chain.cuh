@@ -55,10 +55,10 @@ struct pzs {
 
 // Rounding constants of the three results of a link with larger scale SL:
 // A (scale SL + 1, leading bit 30), B (SL, bit 29), C (SL - 1, rounding 2R).
+// A's mask after halving is ~hA.
 struct alignas(16) pzs_rtab {
   uint32_t hA, hB, hC, pA;  // 2^(p-1) - 1, and A's last kept bit
-  uint32_t mA, mB, mC, pB;  // masks of the kept bits (A's after halving)
-  uint32_t pC, pad0, pad1, pad2;
+  uint32_t mB, mC, pB, pC;  // masks of the kept bits, last kept bits
 };
 
 static __device__ __forceinline__ uint32_t pzs_km(int S) { return (uint32_t)((S >> 2) ^ (S >> 31)); }
@@ -74,10 +74,8 @@ static __device__ __forceinline__ pzs_rtab pzs_rtab_entry(int i) {
   e.hA = (1u << (pA - 1u)) - 1u;
   e.hB = (1u << (pB - 1u)) - 1u;
   e.hC = (1u << (pC - 1u)) - 1u;
-  e.mA = ~e.hA;
   e.mB = ~(2u * e.hB + 1u);
   e.mC = ~(2u * e.hC + 1u);
-  e.pad0 = e.pad1 = e.pad2 = 0u;
   return e;
 }
 
@@ -116,21 +114,49 @@ static __device__ __forceinline__ void pzs_link(pzs &c, pzs t, const pzs_rtab *t
   // the bits shifted out (all of them from 32 on): only whether any is set
   const uint32_t st = min(__funnelshift_rc(0u, (uint32_t)c.m, dC) | __funnelshift_rc(0u, (uint32_t)t.m, dT), 1u);
   const uint4 *ep = reinterpret_cast<const uint4 *>(tab + (SL & 255));
-  const uint4 e0 = ep[0], e1 = ep[1];
-  const uint32_t pC = reinterpret_cast<const uint32_t *>(ep + 2)[0];
-  const uint32_t rB = R + e0.y + (((R >> e1.w) & 1u) | st);
-  const uint32_t mB = rB & e1.y;
+  const uint4 e0 = ep[0], e1 = ep[1];  // hA hB hC pA, mB mC pB pC
+  const uint32_t rB = R + e0.y + (((R >> e1.z) & 1u) | st);
+  const uint32_t mB = rB & e1.x;
   const uint32_t sg = (uint32_t)((int32_t)R >> 31);
   const uint32_t rA = R + e0.x + (((R >> e0.w) & 1u) | st);
-  const uint32_t mA = __funnelshift_r(rA, sg, 1u) & e1.x;  // halved with R's sign
+  const uint32_t mA = __funnelshift_r(rA, sg, 1u) & ~e0.x;  // halved with R's sign
   const uint32_t x2 = R << 1;
-  const uint32_t rC = x2 + e0.z + (((x2 >> pC) & 1u) | st);
-  const uint32_t mC = rC & e1.z;
+  const uint32_t rC = x2 + e0.z + (((x2 >> e1.w) & 1u) | st);
+  const uint32_t mC = rC & e1.y;
   const bool c0 = (R + 0x40000000u) >= 0x80000000u;  // |R| >= 2^30 (R = -2^30: B, the same value)
   const bool c1 = (R + 0x20000000u) >= 0x40000000u;  // |R| >= 2^29
   c.m = (int32_t)(c0 ? mA : (c1 ? mB : mC));
   c.s = c0 ? SL + 1 : (c1 ? SL : SL - 1);
   fmin = min(fmin, R + 0x10000000u);  // below 2^29: |R| < 2^28
+}
+
+// One checked run: the links c (+) pt[0], ..., c (+) pt[cnt - 1] (N > 0: cnt =
+// N, unrolled; N = 0: cnt <= PZS_RUN, rolled).  products_ok: every product is
+// zero or of scale in the band (the caller's check).  The signed form runs
+// when that and the start value allow it; the general addition takes the run
+// (again, from its start) when they do not or when a sum cancelled two or
+// more bits.
+template <int N>
+static __device__ __forceinline__ void pzs_run(pzs &c, const pzs *pt, int cnt, const pzs_rtab *tab,
+                                               bool products_ok) {
+  const pzs save = c;
+  bool general = !products_ok || !pzs_in_band(save);
+  if (!general) {
+    uint32_t fmin = 0xFFFFFFFFu;
+    if (N > 0) {
+#pragma unroll
+      for (int u = 0; u < N; ++u) pzs_link(c, pt[u], tab, fmin);
+    } else {
+#pragma unroll 4
+      for (int u = 0; u < cnt; ++u) pzs_link(c, pt[u], tab, fmin);
+    }
+    general = fmin < 0x20000000u;
+  }
+  if (general) {
+    c = save;
+    const int k = N > 0 ? N : cnt;
+    for (int u = 0; u < k; ++u) c = pzs_link_general(c, pt[u]);
+  }
 }
 
 }  // namespace posit

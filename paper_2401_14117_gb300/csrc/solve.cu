@@ -683,22 +683,8 @@ __global__ void __launch_bounds__(ST, 1) trsv_dot_backward_kernel(const uint32_t
         const pzs *pr = prod[buf];
         const unsigned *bw = bad[buf];
         const int runs = (int)((min64(ST, n - k0) + PZS_RUN - 1) / PZS_RUN);
-        for (int r = 0; r < runs; ++r) {
-          const pzs save = acc;
-          const pzs *pt = pr + PZS_RUN * r;
-          const unsigned bits = bw[r];
-          bool general = (bits != 0u) | !pzs_in_band(save);
-          if (!general) {
-            uint32_t fmin = 0xFFFFFFFFu;
-#pragma unroll
-            for (int u = 0; u < PZS_RUN; ++u) pzs_link(acc, pt[u], tab, fmin);
-            general = fmin < 0x20000000u;
-          }
-          if (general) {
-            acc = save;
-            for (int u = 0; u < PZS_RUN; ++u) acc = pzs_link_general(acc, pt[u]);
-          }
-        }
+        for (int r = 0; r < runs; ++r)
+          pzs_run<PZS_RUN>(acc, pr + PZS_RUN * r, PZS_RUN, tab, bw[r] == 0u);
       }
       __syncthreads();
       buf ^= 1;
