@@ -46,16 +46,19 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // contribute to block I's rows.  One right-hand side is one pipeline of warps:
 //   * the diagonal warp solves the blocks one after another (32 steps:
 //     divide x_t, broadcast it by a shuffle, apply it to the rows after t)
-//     and hands every unknown, as soon as it is final, to
-//   * the next-block warp (same CTA, through shared memory), which brings
-//     block J+1 up to date while block J is solved: tile (J+1, J-1) with the
-//     unknowns of block J-1 (all known), then tile (J+1, J) as block J's
-//     unknowns arrive; it hands block J+1 back to the diagonal warp and
-//     writes block J's unknowns to B;
-//   * helper warps bring every later block I up to date with tiles
-//     (I, 0) .. (I, I-3), each tile as soon as its block's unknowns are
-//     published (a flag per block), and publish block I's partial sums
-//     (another flag) a block-time before the next-block warp needs them.
+//     and posts every unknown, as soon as it is final, in shared memory;
+//   * KS streaming warps (same CTA): while block J is solved, streaming warp
+//     k applies tile (J+k, J) to block J+k as block J's unknowns appear, and
+//     passes block J+k's sums on to warp k-1 (warp 1: to the diagonal warp,
+//     which solves block J+1 next; warp 1 also writes block J's unknowns to
+//     B).  Each warp thus handles one tile per block time and keeps pace
+//     with the diagonal warp; warp KS takes its block's sums from
+//   * helper warps (the other CTAs), which bring every later block I up to
+//     date with tiles (I, 0) .. (I, I-KS-1), each tile as soon as its
+//     block's unknowns are published (a flag per block), and publish block
+//     I's partial sums (another flag).  The streaming warps absorb the
+//     helpers' lag: warp KS may start a tile late and catch up, since the
+//     unknowns it needs are already posted.
 // Every unknown still receives its updates in solve order, one rounded
 // multiply and one rounded subtract each, so the bits equal the sequential
 // loops'.  Solved values and the helpers' partial sums live in B itself.
@@ -65,6 +68,8 @@ __device__ __forceinline__ unsigned long long global_ns() {
 constexpr int PB = 32;       // rows per block
 constexpr int PWARPS = 4;    // warps per CTA
 constexpr int PT = PB * PWARPS;
+constexpr int KS = PWARPS - 1;   // streaming warps: the first CTA but its diagonal warp
+constexpr int kSlotBufs = KS + 1;
 
 struct PipeArgs {
   const uint32_t *A;
@@ -281,22 +286,27 @@ __device__ __forceinline__ pz div_recip(pz x, pz d, uint64_t R) {
 }
 
 // Shared memory of one CTA.  The pipeline's first CTA holds the diagonal
-// warp's tiles D = (J, J) and the next-block warp's tiles C = (J+1, J-1) and
-// S = (J+1, J), each for three blocks (in use, next, being staged); every
-// helper warp stages two tiles.
+// warp's tiles D = (J, J) and each streaming warp's tiles (J+k, J), each for
+// three blocks (in use, next, being staged); in the other CTAs every helper
+// warp stages two tiles.
 constexpr int kTileWords = PB * PB;
 constexpr int kBufs = 3;
-constexpr size_t kPipeSmem = (kBufs * 3 + PWARPS * 2) * kTileWords * sizeof(uint32_t);
+constexpr int kPipeTiles = kBufs * (1 + KS) > 2 * PWARPS ? kBufs * (1 + KS) : 2 * PWARPS;
+constexpr size_t kPipeSmem = (size_t)kPipeTiles * kTileWords * sizeof(uint32_t);
 
-// The diagonal and next-block warps' exchange (static shared memory of the
-// first CTA).  slot[J & 1][s] = (J * 64 + s + 1) << 32 | word of block J's
-// unknown of step s: one 64-bit store carries the value and its tag, so the
-// reader needs no fence.
+// The first CTA's exchange (static shared memory).  slot[J % kSlotBufs][s] =
+// (J * 64 + s + 1) << 32 | word of block J's unknown of step s: one 64-bit
+// store carries the value and its tag, so the reader needs no fence; a
+// buffer is rewritten KS + 1 blocks later, after every streaming warp has
+// read it.  xh[I & 1][k] holds block I's sums from streaming warp k (hand[k]
+// = I once written; taken[k] = I once its reader has copied them, so that
+// the buffer can be reused for block I + 2).
 struct PipeExchange {
-  unsigned long long slot[2][PB];
-  pz xh[PB];        // block J+1's sums through tile J, for the diagonal warp
-  int hand;         // J + 1 once xh holds them
-  int hand_clean;   // their chain is clean
+  unsigned long long slot[kSlotBufs][PB];
+  pz xh[2][KS + 1][PB];
+  int clean[2][KS + 1];  // the chain that produced xh[..][k] stayed in band
+  int hand[KS + 1];
+  int taken[KS + 1];
 };
 
 // Bounded wait of a warp until `cond()` holds (shared-memory polls); false
@@ -334,8 +344,7 @@ __global__ void __launch_bounds__(PT, 1) trsv_pipe_kernel(PipeArgs a) {
   extern __shared__ __align__(16) uint32_t psmem[];
   __shared__ PipeExchange ex;
   const int lane = threadIdx.x & 31;
-  const int wl = threadIdx.x >> 5;                 // warp within the CTA
-  const int w = blockIdx.x * PWARPS + wl;          // warp within the pipeline
+  const int wl = threadIdx.x >> 5;  // warp within the CTA
   const int nblk = a.nblk;
   uint32_t *b = a.B + (int64_t)blockIdx.y * a.ldb;
   int *solved = a.flags + (int64_t)blockIdx.y * 2 * nblk;
@@ -343,20 +352,22 @@ __global__ void __launch_bounds__(PT, 1) trsv_pipe_kernel(PipeArgs a) {
   const unsigned FULL = 0xFFFFFFFFu;
   if (a.abort_flag && *(volatile const int32_t *)a.abort_flag != 0) return;
   if (blockIdx.x == 0) {
-    for (int i = threadIdx.x; i < 2 * PB; i += PT) (&ex.slot[0][0])[i] = 0ull;
-    if (threadIdx.x == 0) ex.hand = 0;
+    for (int i = threadIdx.x; i < kSlotBufs * PB; i += PT) (&ex.slot[0][0])[i] = 0ull;
+    if (threadIdx.x <= KS) {
+      ex.hand[threadIdx.x] = -1;
+      ex.taken[threadIdx.x] = -1;
+    }
   }
   __syncthreads();
 
-  if (w == 0) {
+  if (blockIdx.x == 0 && wl == 0) {
     // ------------------------------------------------ the diagonal warp
     // Solves the blocks one after another: per step, divide x_t, broadcast
     // it, apply it to the rows after t -- straight-line code (every lane
-    // computes, selects keep the lanes that apply) -- and hand x_t to the
-    // next-block warp through shared memory.  A block runs on the in-band
-    // forms while its tile, its chain and the new unknowns qualify; a step
-    // whose unknown leaves the band is redone on the general forms, as is
-    // the rest of that block.
+    // computes, selects keep the lanes that apply) -- and post x_t for the
+    // streaming warps.  A block runs on the in-band forms while its tile,
+    // its chain and the new unknowns qualify; a step whose unknown leaves
+    // the band is redone on the general forms, as is the rest of that block.
     uint32_t *dt = psmem;  // [kBufs][kTileWords]: D of three blocks
     stage_tile<BW>(a, dt, 0, 0);
     asm volatile("cp.async.commit_group;" ::: "memory");
@@ -365,17 +376,19 @@ __global__ void __launch_bounds__(PT, 1) trsv_pipe_kernel(PipeArgs a) {
     pz x = load_x(b, pipe_row0<BW>(0, nblk), a.n);
     bool cx = __all_sync(FULL, pz_band(x, 80));
     for (int J = 0; J < nblk; ++J) {
-      if (J > 0) {  // block J's sums through tile J-1, from the next-block warp
-        if (!warp_spin([&] { return *(volatile int *)&ex.hand >= J; }, a.err)) break;
-        x = ex.xh[lane];
-        cx = *(volatile int *)&ex.hand_clean != 0;
+      if (J > 0) {  // block J's sums through tile J-1, from streaming warp 1
+        if (!warp_spin([&] { return *(volatile int *)&ex.hand[1] >= J; }, a.err)) break;
+        x = ex.xh[J & 1][1][lane];
+        cx = *(volatile int *)&ex.clean[J & 1][1] != 0;
+        __syncwarp();
+        if (lane == 0) *(volatile int *)&ex.taken[1] = J;
       }
       stage_tile<BW>(a, dt + ((J + 2) % kBufs) * kTileWords, J + 2, J + 2);
       asm volatile("cp.async.commit_group;" ::: "memory");
       asm volatile("cp.async.wait_group 1;" ::: "memory");
       __syncwarp();
       const uint32_t *D = dt + (J % kBufs) * kTileWords;
-      unsigned long long *slot = ex.slot[J & 1];
+      unsigned long long *slot = ex.slot[J % kSlotBufs];
       const unsigned long long tag = (unsigned long long)(J * 64) << 32;
       const int64_t row0 = pipe_row0<BW>(J, nblk);
       const int nr = (int)min64(PB, a.n - row0);
@@ -428,144 +441,154 @@ __global__ void __launch_bounds__(PT, 1) trsv_pipe_kernel(PipeArgs a) {
     return;
   }
 
-  if (w == 1) {
-    // ------------------------------------------------ the next-block warp
-    // While the diagonal warp solves block J, brings block J+1 up to date:
-    // its partial sums through tile J-2 come from a helper; tile (J+1, J-1)
-    // uses block J-1's unknowns (known: the products first, then the chain
-    // of additions); tile (J+1, J) takes block J's unknowns from the
-    // exchange slots as they become final.  Then hands block J+1 to the
-    // diagonal warp and writes block J's unknowns to B (flag `solved`).
-    uint32_t *nt = psmem + kBufs * kTileWords;  // [kBufs][C, S][kTileWords]
-    stage_tile<BW>(a, nt, 1, -1);
-    stage_tile<BW>(a, nt + kTileWords, 1, 0);
+  if (blockIdx.x == 0) {
+    // ------------------------------------------------ streaming warp k
+    // While the diagonal warp solves block J, applies tile (J+k, J) to block
+    // J+k as block J's unknowns are posted.  Block J+k's sums through tile
+    // J-1 come from streaming warp k+1 (warp KS: from the helpers; J = 0:
+    // straight from B); its sums through tile J go to warp k-1 (warp 1: to
+    // the diagonal warp).  Warp 1 also writes block J's unknowns to B and
+    // raises `solved[J]` for the helpers.
+    const int k = wl;
+    uint32_t *st = psmem + (size_t)kBufs * k * kTileWords;  // [kBufs][kTileWords]
+    stage_tile<BW>(a, st, k, 0);
     asm volatile("cp.async.commit_group;" ::: "memory");
-    stage_tile<BW>(a, nt + 2 * kTileWords, 2, 0);
-    stage_tile<BW>(a, nt + 3 * kTileWords, 2, 1);
+    stage_tile<BW>(a, st + kTileWords, k + 1, 1);
     asm volatile("cp.async.commit_group;" ::: "memory");
-    pz xprev = pz_zero();  // block J-1's unknowns (lane t: the one of row t)
     for (int J = 0; J < nblk; ++J) {
-      const bool has_next = J + 1 < nblk;
+      const int I = J + k;
+      const bool has = I < nblk;
+      if (!has && k > 1) break;  // nothing left for this warp
       pz xn = pz_zero();
       bool clean = false;
-      if (has_next) {
-        if (J + 1 >= 2) {
-          if (!warp_wait(&ready[J + 1], a.err)) break;
-          clean = __ldcg(&ready[J + 1]) == 1;
-          xn = load_x(b, pipe_row0<BW>(J + 1, nblk), a.n);
-        } else {
-          xn = load_x(b, pipe_row0<BW>(J + 1, nblk), a.n);
+      if (has) {
+        if (J == 0) {
+          xn = load_x(b, pipe_row0<BW>(I, nblk), a.n);
           clean = __all_sync(FULL, pz_band(xn, 80));
+        } else if (k == KS) {
+          if (!warp_wait(&ready[I], a.err)) break;
+          clean = __ldcg(&ready[I]) == 1;
+          xn = load_x(b, pipe_row0<BW>(I, nblk), a.n);
+        } else {
+          if (!warp_spin([&] { return *(volatile int *)&ex.hand[k + 1] >= I; }, a.err)) break;
+          xn = ex.xh[I & 1][k + 1][lane];
+          clean = *(volatile int *)&ex.clean[I & 1][k + 1] != 0;
+          __syncwarp();
+          if (lane == 0) *(volatile int *)&ex.taken[k + 1] = I;
         }
       }
-      uint32_t *nb = nt + ((J + 2) % kBufs) * 2 * kTileWords;
-      stage_tile<BW>(a, nb, J + 3, J + 1);
-      stage_tile<BW>(a, nb + kTileWords, J + 3, J + 2);
+      stage_tile<BW>(a, st + ((J + 2) % kBufs) * kTileWords, J + 2 + k, J + 2);
       asm volatile("cp.async.commit_group;" ::: "memory");
       asm volatile("cp.async.wait_group 1;" ::: "memory");
       __syncwarp();
-      const uint32_t *Cc = nt + (J % kBufs) * 2 * kTileWords, *Sx = Cc + kTileWords;
-      bool tok = pz_band(xprev, 40);
+      const uint32_t *T = st + (J % kBufs) * kTileWords;
+      bool tok = true;
 #pragma unroll 8
-      for (int t = 0; t < PB; ++t) tok &= word_band(Cc[t * PB + lane]) && word_band(Sx[t * PB + lane]);
+      for (int t = 0; t < PB; ++t) tok &= word_band(T[t * PB + lane]);
       clean = clean && __all_sync(FULL, tok);
-      if (has_next) {
-        // tile (J+1, J-1): every product first, then the chain
-        if (clean) {
-          pz p[PB];
-#pragma unroll
-          for (int u = 0; u < PB; ++u) {
-            const int t = BW ? PB - 1 - u : u;
-            uint32_t sg, X0, jam;
-            int S;
-            pz_mul_parts(decode_band(Cc[t * PB + lane]), shfl_pz(xprev, t), sg, S, X0, jam);
-            p[u] = round_band(sg, S, X0 | jam);
-          }
-#pragma unroll
-          for (int u = 0; u < PB; ++u) {
-            uint32_t sg, X;
-            int S;
-            pz_add_exact_inband(xn, pz{p[u].s, p[u].m ^ 0x80000000u}, sg, S, X);
-            xn = round_band(sg, S, X);
-          }
-        } else {
-#pragma unroll 1
-          for (int u = 0; u < PB; ++u) {
-            const int t = BW ? PB - 1 - u : u;
-            xn = msub(xn, Cc[t * PB + lane], shfl_pz(xprev, t));
-          }
-        }
-      }
-      // tile (J+1, J) as block J's unknowns become final
-      const unsigned long long *slot = ex.slot[J & 1];
+      const unsigned long long *slot = ex.slot[J % kSlotBufs];
       pz xcur = pz_zero();
       bool gave_up = false;
+      // the unknowns in groups of SG: wait for the group's last one (they are
+      // posted in order), form the group's products side by side, then run
+      // its chain of subtractions -- a warp that runs behind the diagonal
+      // warp catches up at the products' throughput, not one step's latency
+      constexpr int SG = 8;
 #pragma unroll 1
-      for (int u = 0; u < PB; ++u) {
-        const unsigned long long want = ((unsigned long long)(J * 64 + u + 1)) << 32;
+      for (int g = 0; g < PB; g += SG) {
+        const unsigned long long want = ((unsigned long long)(J * 64 + g + SG)) << 32;
         if (!warp_spin([&] {
-              return (*(volatile const unsigned long long *)&slot[u] & 0xFFFFFFFF00000000ull) ==
-                     want;
+              return (*(volatile const unsigned long long *)&slot[g + SG - 1] &
+                      0xFFFFFFFF00000000ull) == want;
             }, a.err)) {
           gave_up = true;
           break;
         }
-        const pz y = pz_decode((uint32_t)*(volatile const unsigned long long *)&slot[u]);
-        const int t = BW ? PB - 1 - u : u;
-        if (lane == t) xcur = y;
-        if (has_next) {
-          const bool ok = clean && pz_band(y, 40);
-          clean = ok;
-          xn = ok ? msub_band(xn, Sx[t * PB + lane], y) : msub(xn, Sx[t * PB + lane], y);
+        pz y[SG];
+        bool yb = true;
+#pragma unroll
+        for (int v = 0; v < SG; ++v) {
+          y[v] = pz_decode((uint32_t)*(volatile const unsigned long long *)&slot[g + v]);
+          yb &= pz_band(y[v], 40);
+          const int t = BW ? PB - 1 - (g + v) : g + v;
+          if (k == 1 && lane == t) xcur = y[v];
+        }
+        if (!has) continue;
+        if (clean && yb) {
+          pz p[SG];
+#pragma unroll
+          for (int v = 0; v < SG; ++v) {
+            const int t = BW ? PB - 1 - (g + v) : g + v;
+            uint32_t sg, X0, jam;
+            int S;
+            pz_mul_parts(decode_band(T[t * PB + lane]), y[v], sg, S, X0, jam);
+            p[v] = round_band(sg, S, X0 | jam);
+          }
+#pragma unroll
+          for (int v = 0; v < SG; ++v) {
+            uint32_t sg, X;
+            int S;
+            pz_add_exact_inband(xn, pz{p[v].s, p[v].m ^ 0x80000000u}, sg, S, X);
+            xn = round_band(sg, S, X);
+          }
+        } else {
+          clean = false;
+#pragma unroll
+          for (int v = 0; v < SG; ++v) {
+            const int t = BW ? PB - 1 - (g + v) : g + v;
+            xn = msub(xn, T[t * PB + lane], y[v]);
+          }
         }
       }
       if (gave_up) break;
-      if (has_next) {
-        ex.xh[lane] = xn;
-        if (lane == 0) ex.hand_clean = clean;
+      if (has) {
+        // the buffer of this parity last held block I - 2 (if this warp
+        // handed one on): its reader must have copied it
+        if (I - 2 >= k &&
+            !warp_spin([&] { return *(volatile int *)&ex.taken[k] >= I - 2; }, a.err))
+          break;
+        ex.xh[I & 1][k][lane] = xn;
+        if (lane == 0) ex.clean[I & 1][k] = clean;
         __threadfence_block();
         __syncwarp();
-        if (lane == 0) *(volatile int *)&ex.hand = J + 1;
+        if (lane == 0) *(volatile int *)&ex.hand[k] = I;
       }
-      store_x(b, pipe_row0<BW>(J, nblk), a.n, xcur);
-      warp_publish(&solved[J]);
-      xprev = xcur;
+      if (k == 1) {
+        store_x(b, pipe_row0<BW>(J, nblk), a.n, xcur);
+        warp_publish(&solved[J]);
+      }
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     return;
   }
 
   // ---------------------------------------------------- helper warps
-  // Helper h brings blocks I = 2 + h, 2 + h + H, ... up to date with tiles
-  // (I, J) for J <= I - 3, in J order, two blocks at a time (two independent
-  // chains per lane); partial sums stay in B's rows of I.  A tile whose words
-  // and unknowns are all in band, applied to clean chains, runs on the
-  // in-band forms.  Bit k of `dirty` marks the helper's k-th block as not
-  // clean (blocks past the 32nd are treated as not clean).
-  uint32_t *ht = psmem + (kBufs * 3 + wl * 2) * kTileWords;  // [2][kTileWords]
-  const int H = gridDim.x * PWARPS - 2;
-  const int h = w - 2;
+  // Helper h brings blocks I = KS + 1 + h, KS + 1 + h + H, ... up to date
+  // with tiles (I, J) for J <= I - KS - 1, in J order, two blocks at a time
+  // (two independent chains per lane); partial sums stay in B's rows of I.
+  // A tile whose words and unknowns are all in band, applied to clean
+  // chains, runs on the in-band forms.  Bit k of `dirty` marks the helper's
+  // k-th block as not clean (blocks past the 32nd are treated as not clean).
+  uint32_t *ht = psmem + (size_t)wl * 2 * kTileWords;  // [2][kTileWords]
+  const int H = (gridDim.x - 1) * PWARPS;
+  const int h = (blockIdx.x - 1) * PWARPS + wl;
+  const int I0 = KS + 1 + h;
   int Ilast = -1;
-  for (int I = 2 + h; I < nblk; I += H) Ilast = I;
+  for (int I = I0; I < nblk; I += H) Ilast = I;
   if (Ilast < 0) return;
   unsigned dirty = 0;
-  for (int I = 2 + h, k = 0; I <= Ilast; I += H, ++k) {
+  for (int I = I0, kk = 0; I <= Ilast; I += H, ++kk) {
     const bool c = __all_sync(FULL, pz_band(load_x(b, pipe_row0<BW>(I, nblk), a.n), 80));
-    if (!c || k >= 32) dirty |= k < 32 ? (1u << k) : 0u;
+    if (!c || kk >= 32) dirty |= kk < 32 ? (1u << kk) : 0u;
   }
   auto is_clean = [&](int I) {
-    const int k = (I - 2 - h) / H;
-    return k < 32 && !((dirty >> k) & 1u);
+    const int kk = (I - I0) / H;
+    return kk < 32 && !((dirty >> kk) & 1u);
   };
-  if (h == 0) {  // block 2 enters the window unchanged
-    __threadfence();
-    __syncwarp();
-    if (lane == 0) st_release_flag(&ready[2], is_clean(2) ? 1 : 2);
-  }
-  for (int J = 0; J <= Ilast - 3; ++J) {
+  for (int J = 0; J <= Ilast - KS - 1; ++J) {
     const int64_t c0 = pipe_row0<BW>(J, nblk);
-    int I = 2 + h;
-    while (I < J + 3) I += H;
+    int I = I0;
+    while (I < J + KS + 1) I += H;
     bool waited = false;
     for (; I <= Ilast; I += 2 * H) {
       const int I2 = I + H <= Ilast ? I + H : -1;
@@ -611,10 +634,10 @@ __global__ void __launch_bounds__(PT, 1) trsv_pipe_kernel(PipeArgs a) {
           x1 = msub(x1, ht[t * PB + lane], y);
           x2 = msub(x2, ht[kTileWords + t * PB + lane], y);
         }
-        const int k1 = (I - 2 - h) / H;
+        const int k1 = (I - I0) / H;
         if (!ok1 && k1 < 32) dirty |= 1u << k1;
         if (I2 >= 0 && !ok2) {
-          const int k2 = (I2 - 2 - h) / H;
+          const int k2 = (I2 - I0) / H;
           if (k2 < 32) dirty |= 1u << k2;
         }
       }
@@ -623,8 +646,8 @@ __global__ void __launch_bounds__(PT, 1) trsv_pipe_kernel(PipeArgs a) {
       __threadfence();
       __syncwarp();  // the tiles are read before the next pair restages them
       if (lane == 0) {
-        if (J == I - 3) st_release_flag(&ready[I], is_clean(I) ? 1 : 2);
-        if (I2 >= 0 && J == I2 - 3) st_release_flag(&ready[I2], is_clean(I2) ? 1 : 2);
+        if (J == I - KS - 1) st_release_flag(&ready[I], is_clean(I) ? 1 : 2);
+        if (I2 >= 0 && J == I2 - KS - 1) st_release_flag(&ready[I2], is_clean(I2) ? 1 : 2);
       }
     }
   }
@@ -811,13 +834,17 @@ int trsv_pipe(const uint32_t *A, int64_t lda, int trans, int backward, int unit,
   // down to about two blocks per helper they still keep up (two chains per
   // lane), so fewer helpers are used when that lets every right-hand side of
   // the chunk run in one launch.  With fewer co-resident warps than that
-  // each helper takes more blocks (slower, still correct).
+  // each helper takes more blocks (slower, still correct).  The first CTA
+  // holds the diagonal and streaming warps; helpers exist when some block
+  // lies beyond the streaming warps' reach.
   int64_t chunk = min64(min64(NRHS_CHUNK, nrhs),
                         (int64_t)((scratch_bytes - kPipeHead) / per_rhs));
   chunk = max64(1, chunk);
-  const int64_t gx_full = ceil_div(max64(2, nblk - 2) + 2, PWARPS);
-  const int64_t gx_min = ceil_div(max64(2, (nblk - 1) / 2) + 2, PWARPS);
+  const int64_t helpers = max64(0, nblk - KS - 1);
+  const int64_t gx_full = 1 + ceil_div(helpers, PWARPS);
+  const int64_t gx_min = 1 + ceil_div(ceil_div(helpers, 2), PWARPS);
   const int64_t gx = min64(max64(gx_min, min64(gx_full, resident / chunk)), resident);
+  if (helpers > 0 && gx < 2) return POSIT_ERR_DEVICE;  // the helpers need a CTA of their own
   chunk = max64(1, min64(chunk, resident / gx));
   for (int64_t c0 = 0; c0 < nrhs; c0 += chunk) {
     const int64_t nc = min64(chunk, nrhs - c0);
