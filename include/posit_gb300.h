@@ -136,7 +136,10 @@ POSIT_API int posit_rgetrf(int64_t m, int64_t n, posit32_t *A, int64_t lda, int3
  * chain of n(n-1)/2 operations per column); the swaps in reverse order.
  * These are the reference-BLAS trsm orders.  No singularity check: x / 0 is
  * NaR.  Errors: -1 trans, -2 n, -3 nrhs, -4 A NULL, -5 lda, -6 ipiv NULL,
- * -7 B NULL, -8 ldb.
+ * -7 B NULL, -8 ldb.  The environment variable POSIT_SOLVE_SMEM_LIMIT
+ * (bytes), read at each call, caps the shared memory a solve kernel takes
+ * per CTA (this and posit_rpotrs); columns that no longer fit are swapped
+ * and solved by slower global-memory kernels, with the same results.
  * ------------------------------------------------------------------------ */
 POSIT_API int posit_rgetrs(char trans, int64_t n, int64_t nrhs, const posit32_t *A, int64_t lda,
                  const int32_t *ipiv, posit32_t *B, int64_t ldb, cudaStream_t stream);

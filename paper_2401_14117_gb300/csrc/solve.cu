@@ -21,6 +21,8 @@
 //
 // Row swaps (ipiv, LAPACK convention) are applied by a one-CTA-per-column
 // kernel on a shared-memory copy of the column.
+#include <cstdlib>
+
 #include "internal.cuh"
 #include "chain.cuh"
 
@@ -789,10 +791,23 @@ int limits(Limits &l) {
   return POSIT_OK;
 }
 
+// Shared memory a solve kernel may take per CTA: the device's opt-in limit,
+// or less when the environment variable POSIT_SOLVE_SMEM_LIMIT (bytes) says
+// so (room for concurrent kernels; it also makes the global-memory kernels
+// for long columns run at small n).
+size_t solve_smem_cap(const Limits &l) {
+  size_t cap = (size_t)l.smem_optin;
+  if (const char *e = getenv("POSIT_SOLVE_SMEM_LIMIT")) {
+    const long long v = atoll(e);
+    if (v >= 0 && (unsigned long long)v < cap) cap = (size_t)v;
+  }
+  return cap;
+}
+
 int laswp_vec(uint32_t *B, int64_t ldb, int64_t n, int64_t nrhs, const int32_t *ipiv,
               bool reverse, const Limits &l, cudaStream_t stream) {
   size_t smem = (size_t)n * 4;
-  if (smem + 1024 <= (size_t)l.smem_optin) {
+  if (smem + 1024 <= solve_smem_cap(l)) {
     if (cudaFuncSetAttribute(laswp_vec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
       return POSIT_ERR_CUDA;
@@ -868,7 +883,7 @@ int trsv_dot_backward(const uint32_t *A, int64_t lda, int unit, uint32_t *B, int
                       int64_t n, int64_t nrhs, const Limits &l, cudaStream_t stream,
                       const int32_t *abort_flag = nullptr) {
   size_t smem = (size_t)n * sizeof(pz);
-  if (smem + kDotStatic + 1024 <= (size_t)l.smem_optin) {
+  if (smem + kDotStatic + 1024 <= solve_smem_cap(l)) {
     if (cudaFuncSetAttribute(trsv_dot_backward_kernel,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return POSIT_ERR_CUDA;

@@ -456,3 +456,31 @@ def test_solve_fast_path_switches(case, kind):
         binding.posit_rpotrs(uplo, n, nrhs, dF, n, dB, n)
     torch.cuda.synchronize()
     assert_same(from_dev(dB), want, f"{kind} {case}")
+
+@pytest.mark.parametrize("kind", ["getrs_N", "getrs_T", "potrs_L"])
+def test_solve_global_memory_fallbacks(kind, monkeypatch):
+    """Columns too long for one CTA's shared memory (past about 27k rows for the
+    dot-form solve, 57k for the row swaps) are solved and swapped by one-thread
+    kernels in global memory.  POSIT_SOLVE_SMEM_LIMIT caps the shared memory
+    the solve kernels may take, so those kernels run here at n = 300 (ragged,
+    2 right-hand sides) and must give the oracle's words."""
+    monkeypatch.setenv("POSIT_SOLVE_SMEM_LIMIT", "1024")
+    n, nrhs = 300, 2
+    rng = np.random.default_rng(3030 + len(kind))
+    if kind.startswith("getrs"):
+        A = words((n, n), 3100)
+        F, ipiv, _ = oracle.rgetrf(A)
+        B = words((n, nrhs), 3101)
+        want = oracle.rgetrs(F, ipiv, B, trans=kind[-1])
+        dF, dB = to_dev(F), to_dev(B)
+        dp = torch.from_numpy(ipiv.astype(np.int32)).to(DEV)
+        binding.posit_rgetrs(kind[-1], n, nrhs, dF, n, dp, dB, n)
+    else:
+        F, _ = oracle.rpotrf(spd_words(n, 3102), uplo="L")
+        B = words((n, nrhs), 3103)
+        B[rng.integers(0, n), 1] = 0x80000000  # a NaR right-hand side entry
+        want = oracle.rpotrs(F, B, uplo="L")
+        dF, dB = to_dev(F), to_dev(B)
+        binding.posit_rpotrs("L", n, nrhs, dF, n, dB, n)
+    torch.cuda.synchronize()
+    assert_same(from_dev(dB), want, kind)
