@@ -295,6 +295,12 @@ constexpr int kTileWords = PB * PB;
 constexpr int kBufs = 3;
 constexpr int kPipeTiles = kBufs * (1 + KS) > 2 * PWARPS ? kBufs * (1 + KS) : 2 * PWARPS;
 constexpr size_t kPipeSmem = (size_t)kPipeTiles * kTileWords * sizeof(uint32_t);
+// Dynamic shared memory requested per CTA: more than the tiles need, so that
+// at most two CTAs share an SM (with up to four, a pipeline's first CTA shares
+// its SM's schedulers with helper CTAs: 8 right-hand sides at n = 8192 took
+// 12.6 ms against 9.4 with two and 14.1 with one, when too few helpers fit).
+constexpr size_t kPipeLaunchSmem = 76 * 1024;
+static_assert(kPipeLaunchSmem >= kPipeSmem, "the launch covers the tiles");
 
 // The first CTA's exchange (static shared memory).  slot[J % kSlotBufs][s] =
 // (J * 64 + s + 1) << 32 | word of block J's unknown of step s: one 64-bit
@@ -417,9 +423,10 @@ __global__ void __launch_bounds__(PT, 1) trsv_pipe_kernel(PipeArgs a) {
           xs = pz{up ? r.s : xs.s, up ? r.m : xs.m};
           if (!pz_band(xt, 40)) break;  // the same on every lane: redo this step below
           x = xs;
-          if (lane == 0)
-            *(volatile unsigned long long *)&slot[s] =
-                tag + ((unsigned long long)(s + 1) << 32) + bits_band(xt);
+          // every lane stores the same word (xt came from one lane): no
+          // divergent branch on the step's path
+          *(volatile unsigned long long *)&slot[s] =
+              tag + ((unsigned long long)(s + 1) << 32) + bits_band(xt);
         }
       }
 #pragma unroll 1
@@ -434,9 +441,8 @@ __global__ void __launch_bounds__(PT, 1) trsv_pipe_kernel(PipeArgs a) {
         const pz r = msub(x, D[t * PB + lane], xt);
         const bool up = (BW ? lane < t : lane > t) && lane < nr;
         x = pz{up ? r.s : x.s, up ? r.m : x.m};
-        if (lane == 0)
-          *(volatile unsigned long long *)&slot[s] =
-              tag + ((unsigned long long)(s + 1) << 32) + pz_to_bits(xt);
+        *(volatile unsigned long long *)&slot[s] =
+            tag + ((unsigned long long)(s + 1) << 32) + pz_to_bits(xt);
       }
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -837,11 +843,11 @@ int trsv_pipe(const uint32_t *A, int64_t lda, int trans, int backward, int unit,
                                     : (const void *)trsv_pipe_kernel<true, false>)
                             : (unit ? (const void *)trsv_pipe_kernel<false, true>
                                     : (const void *)trsv_pipe_kernel<false, false>);
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPipeSmem) !=
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPipeLaunchSmem) !=
       cudaSuccess)
     return POSIT_ERR_CUDA;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PT, kPipeSmem) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PT, kPipeLaunchSmem) != cudaSuccess ||
       per_sm < 1)
     return POSIT_ERR_CUDA;
   const int64_t resident = (int64_t)per_sm * l.sms;
@@ -873,7 +879,7 @@ int trsv_pipe(const uint32_t *A, int64_t lda, int trans, int backward, int unit,
     pa.abort_flag = abort_flag;
     void *args[] = {&pa};
     if (cudaLaunchCooperativeKernel(fn, dim3((unsigned)gx, (unsigned)nc), dim3(PT), args,
-                                    kPipeSmem, stream) != cudaSuccess)
+                                    kPipeLaunchSmem, stream) != cudaSuccess)
       return POSIT_ERR_CUDA;
   }
   return POSIT_OK;
